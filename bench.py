@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark of the RTM hot path on GB300.
+
+One bench step is one full RTM shot of the single-shot throughput workload:
+512^3 model (576^3 padded with a 32-cell sponge), 8th-order stencil, smooth
+random velocity (1500-4500 m/s, sigma 8), 2000 steps, 20 Hz Ricker at the
+surface centre, 512 x 512 receivers at depth index 2, checkpoints every 50
+steps: forward modelling with checkpoints, then per segment a recompute with
+snapshot writes and the receiver propagation with the imaging condition fused
+into the backward stencil. The metric is stencil point-updates per second over
+all three passes (3 x 2000 x 576^3 per shot).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (under torchrun) every rank runs its own shot (weak scaling); the
+timing is the slowest rank's. ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpoint-updates/s vs HBM roofline; RTM shot time learned vs checkpoint @≤1e-2"
+UNIT = "Gpoint-updates/s"
+PROFILE = os.path.join(ROOT, "profiles", "stencil_bwd_image_r4_smooth512.md")
+STENCIL_SRC = os.path.join(ROOT, "paper_1603_03971_gb300", "csrc", "stencil.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="smooth_512")
+    ap.add_argument("--nt", type=int, default=0, help="override the step count (testing only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-steps", type=int, default=2,
+                    help="oracle time steps per bench step of the reference arm")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(args):
+    import rtm_inputs
+
+    w = rtm_inputs.WORKLOADS[args.workload]
+    if args.nt:
+        w = w.scaled(nt=args.nt)
+    return w
+
+
+def config_of(w):
+    NZ, NY, NX = w.padded_shape
+    return {
+        "workload": "%s: %dx%dx%d model (%dx%dx%d padded), r=%d stencil, %d steps, "
+                    "%s velocity, %.0f Hz Ricker, %dx%d receivers, checkpoint every %d"
+                    % (w.name, w.nx, w.ny, w.nz, NX, NY, NZ, w.radius, w.nt, w.velocity,
+                       w.f0, w.nx, w.ny, w.ckpt_every),
+        "grid": [w.nx, w.ny, w.nz],
+        "padded": [NX, NY, NZ],
+        "radius": w.radius,
+        "nt": w.nt,
+        "ckpt_every": w.ckpt_every,
+        "updates_per_shot": 3 * w.nt * NX * NY * NZ,
+        "l2": "inputs larger than L2 (each field %.0f MB > 129 MB L2)" % (NX * NY * NZ * 4 / 1e6),
+    }
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import torch
+
+            ident = str(self.dev)
+            uuid = getattr(torch.cuda.get_device_properties(self.dev), "uuid", None)
+            if uuid is not None:
+                u = str(uuid)
+                ident = u if u.startswith("GPU-") else "GPU-" + u
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", ident, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            out["reasons"] = ["unsampled"]
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            out["reasons"] = ["unsampled"]
+            return out
+        sm = sorted(float(r[1]) for r in rows if re.match(r"^[\d.]+$", r[1]))
+        mx = [float(r[2]) for r in rows if re.match(r"^[\d.]+$", r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for i, n in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        out.update(sm_mhz=sm[len(sm) // 2] if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+# ----------------------------------------------------------------------------
+# roofline helpers
+# ----------------------------------------------------------------------------
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the backward imaging stencil from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    if not os.path.exists(PROFILE):
+        return None
+    text = open(PROFILE).read()
+    m_t = re.search(r"traffic_bytes_per_launch:\s*([\d.eE+]+)", text)
+    m_h = re.search(r"stencil_source_sha256:\s*([0-9a-f]{64})", text)
+    if not (m_t and m_h):
+        return None
+    cur = hashlib.sha256(open(STENCIL_SRC, "rb").read()).hexdigest()
+    if cur != m_h.group(1):
+        return None
+    return float(m_t.group(1))
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (baseline and reference arm)
+# ----------------------------------------------------------------------------
+
+def oracle_sample(w, vel_np, steps: int):
+    """Time ``steps`` forward time steps of the FP64 oracle on the full padded
+    grid of the workload; returns (seconds, updates, threads)."""
+    import numpy as np
+
+    import oracle
+
+    rec = w.receivers()[:1]
+    p = oracle.Problem(vel_np, w.nb, w.radius, w.dx, w.dt, steps, w.f0, w.t0, w.src, rec)
+    t = time.perf_counter()
+    p.forward()
+    el = time.perf_counter() - t
+    NZ, NY, NX = w.padded_shape
+    del p
+    np.zeros(1)
+    return el, steps * NX * NY * NZ, oracle.num_threads()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    w = workload(args)
+    vel = w.velocity_model(device=None) if w.nx <= 256 else None
+    if vel is None:
+        import torch
+
+        dev = "cuda" if torch.cuda.is_available() else None
+        v = w.velocity_model(device=dev)
+        vel = v.double().cpu().numpy() if hasattr(v, "cpu") else v
+    vel = np.asarray(vel, dtype=np.float64)
+    NZ, NY, NX = w.padded_shape
+    for _ in range(args.warmup):
+        oracle_sample(w, vel, args.ref_steps)
+    total_s, total_u, threads = 0.0, 0, 1
+    for _ in range(args.steps):
+        s, u, threads = oracle_sample(w, vel, args.ref_steps)
+        total_s += s
+        total_u += u
+    value = total_u / total_s / 1e9
+    sample = ("%d forward time steps of the FP64 oracle on the %dx%dx%d padded grid per bench "
+              "step" % (args.ref_steps, NX, NY, NZ))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(w),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1603_03971_gb300 as rtm
+    from paper_1603_03971_gb300 import shots
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = workload(args)
+    cfg = config_of(w)
+    NZ, NY, NX = w.padded_shape
+    src = shots.shot_source(rank, world, w.nx, w.ny, w.src[2]) if world > 1 else w.src
+    p = rtm.params_for(w, src=src)
+    rec_np = w.receivers()
+    rec = torch.from_numpy(rec_np).to(dev)
+    vel = w.velocity_model(device=dev).contiguous()
+    ws = rtm.alloc_workspace(p, dev, host_io=True)
+    c = rtm.model_prep(p, vel, ws)
+
+    # synthetic observed data: the modelled data of this shot
+    dobs = torch.empty((w.nt, p.nrec), dtype=torch.float32, device=dev)
+    rtm.forward(p, c, rec, ws, data=dobs)
+    rtm.check(ws)
+    image = torch.zeros((w.nz, w.ny, w.nx), dtype=torch.float32, device=dev)
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        rtm.shot(p, c, rec, dobs, ws, image)
+    rtm.check(ws)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    sampler = ClockSampler(local)
+    rtm.reset_stats()
+    rtm.set_timing(True)
+    sampler.start()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        rtm.shot(p, c, rec, dobs, ws, image)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    rtm.set_timing(False)
+    st = rtm.stats()
+    rtm.check(ws)
+    t_local = e0.elapsed_time(e1) / 1e3
+    t_max = shots.max_over_ranks(t_local, device=dev)
+    updates = cfg["updates_per_shot"]
+    value = updates * args.steps * world / t_max / 1e9
+
+    # roofline of the dominant kernel: the backward stencil with fused imaging
+    hbm, peak_kind = measured_peaks()
+    b = st["stencil"]["bwd_image"]
+    launches = b["launches"]
+    per_launch_bytes = b["bytes"] / max(launches, 1)
+    per_launch_s = b["ms"] / max(launches, 1) / 1e3
+    achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else None
+    shares = {k: v["ms"] for k, v in st["stencil"].items() if v["launches"]}
+    roofline = {
+        "kernel": "k_stencil<4, MODE_BWD_IMAGE> (backward step + fused zero-lag imaging)",
+        "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+        "frac": (achieved / hbm) if achieved else None, "peak_kind": peak_kind,
+        "traffic": profiled_traffic(), "algorithmic_bytes_per_launch": per_launch_bytes,
+        "launch_ms": per_launch_s * 1e3,
+        "stencil_ms_per_step": {k: v / args.steps for k, v in shares.items()},
+    }
+
+    # end to end: host buffers through rtm_shot_host
+    e2e = None
+    if not args.no_e2e:
+        v_h = vel.cpu().pin_memory()
+        rec_h = torch.from_numpy(rec_np).pin_memory()
+        dobs_h = dobs.cpu().pin_memory()
+        img_h = torch.empty((w.nz, w.ny, w.nx), dtype=torch.float32).pin_memory()
+        rtm.shot_host(p, v_h, rec_h, dobs_h, img_h, ws)
+        k_e2e = max(1, min(args.steps, 2))
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            rtm.shot_host(p, v_h, rec_h, dobs_h, img_h, ws)
+        t_e2e = shots.max_over_ranks(time.perf_counter() - t0, device=dev)
+        h2d = v_h.numel() * 4 + rec_h.numel() * 4 + dobs_h.numel() * 4
+        e2e = {"value": updates * k_e2e * world / t_e2e / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(img_h.numel() * 4),
+               "steps": k_e2e, "s_per_step": t_e2e / k_e2e}
+        del v_h, dobs_h
+
+    if world > 1:
+        shots.stack_images(image)  # the multi-shot stack (outside the timed region)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        vel64 = vel.double().cpu().numpy()
+        del ws
+        torch.cuda.empty_cache()
+        steps = 10 if NX * NY * NZ > 50_000_000 else 50
+        s, u, threads = oracle_sample(w, vel64, steps)
+        cpu = {"value": u / s / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "%d forward time steps of the FP64 oracle on the %dx%dx%d padded "
+                         "grid (%.1f s)" % (steps, NX, NY, NZ, s)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded smooth random velocity; observed data modelled on it)",
+            "config": cfg, "shot_s": t_max / args.steps, "roofline": roofline,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": st["launches"],
+            "clocks": clocks, "impl": "ours",
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,208 @@
+/*
+ * librtm -- C ABI of the GB300 (sm_103a) RTM hot path.
+ *
+ * The method: reverse time migration as the paper describes it (Sec. I):
+ * pressure waves are simulated forward from the source and backward from the
+ * recorded data, and the two wavefields are correlated into an image. The
+ * solver applies a high-order stencil to a 3D block in every time step
+ * (Sec. II). The paper gives no formulas; the discrete method implemented
+ * here is:
+ *
+ *   L u       = sum over x, y, z of [a0 u + sum_{k=1..r} a_k (u_{+k} + u_{-k})] / dx^2
+ *               (2r-order central weights, zero ghost cells outside the padded grid)
+ *   u^{n+1}   = g (2 u^n + c L u^n) - g^2 u^{n-1},   c = v^2 dt^2,  g = gx gy gz
+ *   u^{n+1}[s]  += c[s] w(n dt) / dx^3,   w = Ricker(f0, t0)
+ *   d[n][j]   = u^{n+1}[rec_j]
+ *   mu^m      = g (2 mu^{m+1} + c L mu^{m+1}) - g^2 mu^{m+2},  m = nt..1  (mu^{nt+1} = mu^{nt+2} = 0)
+ *   mu^m[rec_j] += c g r^{m-1}_j / dx^3
+ *   I(x)     += u^m(x) mu^m(x)    on the model region, for m % image_every == 0
+ *
+ * with a sponge g_a(d) = exp(-(0.015 (nb - d))^2) for cells at distance
+ * d < nb from an outer face and 1 elsewhere. The backward recursion is the
+ * exact transpose of the forward one in the scaled variable
+ * mu = C G lambda / dx^3, so the same kernel runs in both directions.
+ *
+ * Conventions for every call:
+ *  - Grids are float32, C order [z][y][x], x contiguous (the x-innermost
+ *    loop order the paper settles on in Sec. III).
+ *  - The model grid is nx * ny * nz. The padded (computational) grid adds nb
+ *    sponge cells on all six faces: NX = nx + 2 nb, etc. NX must be a
+ *    multiple of 4 so that every row starts on a 16-byte boundary.
+ *  - Every array argument is caller-owned memory. Pointers named d_* are
+ *    device pointers, h_* host pointers. The library never allocates device
+ *    memory and never frees caller memory: all scratch lives in the caller's
+ *    workspace (the paper's lesson of passing pointers instead of copying
+ *    data, Sec. III). Device pointers must be 16-byte aligned; the workspace
+ *    256-byte aligned.
+ *  - Calls are asynchronous on the given stream (NULL = legacy default
+ *    stream) unless stated otherwise. Host-side argument checks run before any
+ *    launch and return RTM_ERR_INVALID without touching the device.
+ *    Device-side checks (receiver coordinates out of range, bounded waits)
+ *    write a status word in the workspace; rtm_check() reads and clears it.
+ *    rtm_forward and rtm_shot clear it when they start, so it reports the
+ *    device-side errors of the pipeline started by the latest forward pass.
+ *  - On any error the thread-local message of rtm_last_error() says why.
+ */
+#ifndef RTM_H
+#define RTM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *rtm_stream; /* the same handle as cudaStream_t */
+
+typedef enum {
+    RTM_OK = 0,
+    RTM_ERR_INVALID = 1,     /* an argument is out of range */
+    RTM_ERR_CFL = 2,         /* dt above the leapfrog stability limit */
+    RTM_ERR_WORKSPACE = 3,   /* workspace missing, too small or misaligned */
+    RTM_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    RTM_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out */
+    RTM_ERR_NUMERIC = 6,     /* non-finite or non-positive model values */
+    RTM_ERR_UNSUPPORTED = 7, /* e.g. a stencil radius other than 4 or 8 */
+    RTM_ERR_STATE = 8        /* workspace prepared for another purpose */
+} rtm_status;
+
+enum { RTM_STORE_ALL = 0, RTM_STORE_CKPT = 1 };
+enum { RTM_VEL_V = 0, RTM_VEL_V2 = 1 };
+
+typedef struct {
+    int32_t nx, ny, nz;     /* model grid */
+    int32_t nb;             /* sponge width (cells, each face) */
+    int32_t radius;         /* stencil radius r: 4 (8th order) or 8 (16th order) */
+    int32_t nt;             /* time steps */
+    double dx;              /* grid spacing (m) */
+    double dt;              /* time step (s) */
+    double f0;              /* Ricker peak frequency (Hz) */
+    double t0;              /* Ricker delay (s) */
+    int32_t src_x, src_y, src_z; /* source, model coordinates in [-nb, n + nb) */
+    int32_t nrec;           /* receivers */
+    int32_t storage;        /* RTM_STORE_ALL: keep every imaging snapshot;
+                               RTM_STORE_CKPT: checkpoints + segment recompute */
+    int32_t ckpt_every;     /* steps per checkpoint segment (RTM_STORE_CKPT) */
+    int32_t image_every;    /* image at steps m with m % image_every == 0 (>= 1) */
+    int32_t want_grad;      /* 1: prepare the workspace for rtm_grad instead of imaging */
+} rtm_params;
+
+/* Per-kernel-class device time, filled when timing is enabled. */
+typedef struct {
+    int64_t launches;       /* kernel launches of this library since the last reset */
+    int64_t stencil_launches[6];  /* per stencil mode: fwd, fwd+snap, bwd+image,
+                                     fwd+Lu, bwd+grad, batched */
+    double stencil_ms[6];   /* summed CUDA-event time per stencil mode */
+    double stencil_bytes[6];/* summed algorithmic bytes per stencil mode */
+} rtm_stats;
+
+/* Library version string. */
+const char *rtm_version(void);
+
+/* Thread-local description of the last error returned on this thread. */
+const char *rtm_last_error(void);
+
+/* Host-only argument checks of a parameter block (no device access). */
+rtm_status rtm_validate(const rtm_params *p);
+
+/* Workspace bytes that rtm_forward / rtm_backward_image / rtm_shot / rtm_grad
+ * need for p (0 if p is invalid). The same workspace must be passed to the
+ * forward call and to the backward call that consumes its snapshots or
+ * checkpoints. */
+size_t rtm_workspace_size(const rtm_params *p);
+
+/* Model preparation (the padded coefficient grid).
+ *   d_vel  [nz][ny][nx] velocity (vel_kind RTM_VEL_V, m/s) or squared
+ *          velocity (RTM_VEL_V2, m^2/s^2) on the model grid.
+ *   d_c    [NZ][NY][NX] out: c = v^2 dt^2, each padded cell copying the
+ *          nearest model cell.
+ *   d_ws   any workspace of at least 256 bytes (its status block holds the
+ *          reduction words).
+ * Computes max v on the device and SYNCHRONISES the stream to check the
+ * leapfrog stability limit vmax dt / dx <= 2 / sqrt(3 |S(pi)|) with
+ * S(theta) = a0 + 2 sum_k a_k cos(k theta) (0.4529 for r = 4, 0.4237 for
+ * r = 8): RTM_ERR_CFL if violated, RTM_ERR_NUMERIC if a value is not finite
+ * and positive. */
+rtm_status rtm_model_prep(const rtm_params *p, const float *d_vel, int32_t vel_kind,
+                          float *d_c, void *d_ws, size_t ws_bytes, rtm_stream stream);
+
+/* Forward modelling from zero initial fields.
+ *   d_c     [NZ][NY][NX] coefficient grid from rtm_model_prep.
+ *   d_rec   [nrec][3] int32 receiver model coordinates (x, y, z), each in
+ *           [-nb, n + nb); receivers outside are skipped and flagged.
+ *   d_data  [nt][nrec] out: d[n][j] = u^{n+1}[rec_j]; may be NULL.
+ *   d_ws    workspace of rtm_workspace_size(p) bytes; receives the imaging
+ *           snapshots (RTM_STORE_ALL) or the checkpoints (RTM_STORE_CKPT).
+ *   d_u_last [2][NZ][NY][NX] out: u^{nt-1}, u^{nt}; may be NULL. */
+rtm_status rtm_forward(const rtm_params *p, const float *d_c, const int32_t *d_rec,
+                       float *d_data, void *d_ws, size_t ws_bytes, float *d_u_last,
+                       rtm_stream stream);
+
+/* Receiver propagation backward in time with the zero-lag imaging condition
+ * fused into the backward stencil. Needs a preceding rtm_forward with the same
+ * p, d_c, d_rec and d_ws on the same stream (want_grad = 0).
+ *   d_rdata   [nt][nrec] data injected at the receivers (RTM: the recorded data).
+ *   d_image   [nz][ny][nx] model grid, ACCUMULATED (+=), so shots sum.
+ *   d_src_adj [nt] out: mu^{n+1}[s] / g_s, the transpose of the forward map
+ *             evaluated on d_rdata (for dot-product tests); may be NULL. */
+rtm_status rtm_backward_image(const rtm_params *p, const float *d_c, const int32_t *d_rec,
+                              const float *d_rdata, void *d_ws, size_t ws_bytes,
+                              float *d_image, float *d_src_adj, rtm_stream stream);
+
+/* One RTM shot: rtm_forward then rtm_backward_image of d_dobs.
+ *   d_data  [nt][nrec] out: the modelled data; may be NULL. */
+rtm_status rtm_shot(const rtm_params *p, const float *d_c, const int32_t *d_rec,
+                    const float *d_dobs, float *d_data, void *d_ws, size_t ws_bytes,
+                    float *d_image, rtm_stream stream);
+
+/* Gradient of J = 1/2 ||d - d_obs||^2 with respect to v^2 on the model grid,
+ * given the residual d - d_obs. Needs a preceding rtm_forward with the same
+ * p (want_grad = 1), d_c, d_rec and d_ws on the same stream.
+ *   d_resid   [nt][nrec] residual r = d - d_obs.
+ *   d_grad_v2 [nz][ny][nx] out (overwritten): dJ/d(v^2)
+ *             = dt^2 * fold(dx^3 / c * sum_n mu^{n+1} (L u^n + [s] w^n / (dx^3 g_s))),
+ *             fold = transpose of the edge padding. */
+rtm_status rtm_grad(const rtm_params *p, const float *d_c, const int32_t *d_rec,
+                    const float *d_resid, void *d_ws, size_t ws_bytes, float *d_grad_v2,
+                    rtm_stream stream);
+
+/* Misfit: d_resid[i] = d_data[i] - d_obs[i]; *d_J = 1/2 sum d_resid^2
+ * accumulated in float64 (overwritten). d_resid may be NULL. */
+rtm_status rtm_misfit(const float *d_data, const float *d_obs, int64_t n, float *d_resid,
+                      double *d_J, rtm_stream stream);
+
+/* Workspace bytes for rtm_shot_host: rtm_workspace_size(p) plus device room
+ * for the velocity, coefficients, receivers, data and image. */
+size_t rtm_host_workspace_size(const rtm_params *p);
+
+/* One RTM shot from HOST buffers, end to end: copies h_vel [nz][ny][nx],
+ * h_rec [nrec][3] and h_dobs [nt][nrec] to the device workspace, prepares the
+ * model, runs the shot and copies the image [nz][ny][nx] back into h_image
+ * (overwritten). Pinned host memory makes the copies asynchronous. Returns
+ * after the stream has been synchronised. */
+rtm_status rtm_shot_host(const rtm_params *p, const float *h_vel, int32_t vel_kind,
+                         const int32_t *h_rec, const float *h_dobs, float *h_image,
+                         void *d_ws, size_t ws_bytes, rtm_stream stream);
+
+/* Synchronise the stream, read and clear the device status word of the
+ * workspace: RTM_OK, RTM_ERR_INVALID (a receiver out of range was skipped),
+ * RTM_ERR_TIMEOUT (a bounded wait ran out) or RTM_ERR_CUDA. */
+rtm_status rtm_check(void *d_ws, size_t ws_bytes, rtm_stream stream);
+
+/* Stencil tuning: z extent of the slab one thread block marches through
+ * (0 = automatic) and the plane-load path (0 = automatic, 1 = vector loads
+ * through registers, 2 = TMA). Applies to later calls on every thread. */
+rtm_status rtm_set_tuning(int32_t radius, int32_t zchunk, int32_t variant);
+
+/* Enable (1) or disable (0) per-launch CUDA-event timing of the stencil
+ * kernels. While enabled, each API call synchronises its stream on return. */
+rtm_status rtm_set_timing(int32_t enable);
+rtm_status rtm_stats_get(rtm_stats *out);
+rtm_status rtm_stats_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RTM_H */

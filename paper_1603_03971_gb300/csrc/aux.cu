@@ -1,0 +1,274 @@
+// Small kernels around the stencil: model preparation, sponge profiles, the
+// Ricker wavelet, source injection / receiver gather, adjoint injection,
+// image and gradient finalisation, and the data misfit.
+
+#include <math.h>
+
+#include "rtm_internal.h"
+
+namespace rtm {
+
+namespace {
+
+constexpr int kStatusInvalid = 1;  // == RTM_ERR_INVALID
+
+__device__ __forceinline__ void flag(int* status, int code) {
+    if (status) atomicCAS(status, 0, code);
+}
+
+// padded linear index of model coordinates (x, y, z), or -1 if outside the
+// padded grid
+__device__ __forceinline__ long long rec_index(const Geometry& G, const int32_t* rec, int j) {
+    const int x = rec[3 * j + 0] + G.nb, y = rec[3 * j + 1] + G.nb, z = rec[3 * j + 2] + G.nb;
+    if (x < 0 || x >= G.NX || y < 0 || y >= G.NY || z < 0 || z >= G.NZ) return -1;
+    return ((long long)z * G.NY + y) * G.NX + x;
+}
+
+__device__ __forceinline__ float sponge_at(const Geometry& G, const float* gx, const float* gy,
+                                           const float* gz, long long i) {
+    const long long plane = (long long)G.NX * G.NY;
+    const int z = (int)(i / plane);
+    const int y = (int)((i % plane) / G.NX);
+    const int x = (int)(i % G.NX);
+    return gx[x] * gy[y] * gz[z];
+}
+
+// Cerjan-type profile: exp(-(0.015 (nb - d))^2) within nb cells of a face
+__device__ __forceinline__ float sponge_1d(int i, int n, int nb) {
+    const int d = min(i, n - 1 - i);
+    if (d >= nb) return 1.0f;
+    const double s = 0.015 * (double)(nb - d);
+    return (float)exp(-s * s);
+}
+
+__global__ void k_sponge(Geometry G, float* gx, float* gy, float* gz) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < G.NX) gx[i] = sponge_1d(i, G.NX, G.nb);
+    if (i < G.NY) gy[i] = sponge_1d(i, G.NY, G.nb);
+    if (i < G.NZ) gz[i] = sponge_1d(i, G.NZ, G.nb);
+}
+
+// Ricker: w(t) = (1 - 2 pi^2 f0^2 (t - t0)^2) exp(-pi^2 f0^2 (t - t0)^2), in double
+__global__ void k_wavelet(int nt, double dt, double f0, double t0, float* w) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nt) return;
+    const double pf = 3.14159265358979323846 * f0 * ((double)n * dt - t0);
+    const double a = pf * pf;
+    w[n] = (float)((1.0 - 2.0 * a) * exp(-a));
+}
+
+// c = v^2 dt^2 on the padded grid (edge padding); max v^2 and validity over
+// the model cells
+__global__ void k_model_prep(Geometry G, const float* __restrict__ vel, int squared, float dt2,
+                             float* __restrict__ c, unsigned int* vmax_bits, int* bad) {
+    const long long N = (long long)G.NX * G.NY * G.NZ;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    float local_max = 0.0f;
+    int local_bad = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const long long plane = (long long)G.NX * G.NY;
+        const int z = (int)(i / plane);
+        const int y = (int)((i % plane) / G.NX);
+        const int x = (int)(i % G.NX);
+        const int mx = min(max(x - G.nb, 0), G.nx - 1);
+        const int my = min(max(y - G.nb, 0), G.ny - 1);
+        const int mz = min(max(z - G.nb, 0), G.nz - 1);
+        const float v = vel[((long long)mz * G.ny + my) * G.nx + mx];
+        const float v2 = squared ? v : v * v;
+        c[i] = v2 * dt2;
+        const bool interior = (x - G.nb == mx) && (y - G.nb == my) && (z - G.nb == mz);
+        if (interior) {
+            if (!(isfinite(v) && v > 0.0f)) local_bad = 1;
+            else local_max = fmaxf(local_max, v2);
+        }
+    }
+    // warp reduction then one atomic per warp
+    for (int o = 16; o > 0; o >>= 1) {
+        local_max = fmaxf(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+        local_bad |= __shfl_xor_sync(0xffffffffu, local_bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(vmax_bits, __float_as_uint(local_max));  // non-negative floats order as uints
+        if (local_bad) atomicOr(bad, 1);
+    }
+}
+
+__global__ void k_fwd_aux(Geometry G, const float* __restrict__ u_cur, float* u_prev,
+                          const float* __restrict__ c, const float* gx, const float* gy,
+                          const float* gz, const int32_t* __restrict__ rec, int nrec,
+                          float* data_row, long long src, const float* w_n, float inv_dx3,
+                          int* status) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < nrec) {
+        if (data_row) {
+            const long long i = rec_index(G, rec, j);
+            if (i < 0) flag(status, kStatusInvalid);
+            data_row[j] = i >= 0 ? u_cur[i] : 0.0f;
+        }
+    } else if (j == nrec && w_n) {
+        // the stencil computes g(...) - g^2 u_prev: lowering u_prev[s] by
+        // c_s w / (dx^3 g_s^2) adds c_s w / dx^3 to u^{n+1}[s]
+        const float g = sponge_at(G, gx, gy, gz, src);
+        u_prev[src] -= c[src] * (*w_n) * inv_dx3 / (g * g);
+    }
+}
+
+__global__ void k_bwd_aux(Geometry G, const float* __restrict__ mu_cur, float* mu_prev,
+                          const float* __restrict__ c, const float* gx, const float* gy,
+                          const float* gz, const int32_t* __restrict__ rec, int nrec,
+                          const float* __restrict__ r_row, long long src, float* src_adj_slot,
+                          float* grad_acc, const float* w_n, float inv_dx3, int* status) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < nrec) {
+        if (r_row) {
+            const long long i = rec_index(G, rec, j);
+            if (i < 0) {
+                flag(status, kStatusInvalid);
+            } else {
+                // lowering mu_prev[i] by c r / (dx^3 g) adds c g r / dx^3 to mu^m[i]
+                const float g = sponge_at(G, gx, gy, gz, i);
+                atomicAdd(&mu_prev[i], -c[i] * r_row[j] * inv_dx3 / g);
+            }
+        }
+    } else if (j == nrec) {
+        const float g = sponge_at(G, gx, gy, gz, src);
+        const float m = mu_cur[src];
+        if (src_adj_slot) *src_adj_slot = m / g;
+        if (grad_acc && w_n) grad_acc[src] += m * (*w_n) * inv_dx3 / g;
+    }
+}
+
+__global__ void k_image_finalize(Geometry G, const float* __restrict__ slab,
+                                 float* __restrict__ image) {
+    const long long n = (long long)G.nx * G.ny * G.nz;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const long long zy = i / G.nx;
+        const int x = (int)(i % G.nx);
+        image[i] += slab[zy * G.NX + x + G.nb];
+    }
+}
+
+__device__ __forceinline__ void fold_range(int m, int n, int nb, int N, int& lo, int& hi) {
+    lo = (m == 0) ? 0 : m + nb;
+    hi = (m == n - 1) ? N - 1 : m + nb;
+}
+
+// grad_v2[model cell] = dt^2 * sum over the padded cells copied from that
+// cell of dx^3 acc / c (the transpose of the edge padding)
+__global__ void k_grad_finalize(Geometry G, const float* __restrict__ acc,
+                                const float* __restrict__ c, double dx3, double dt2,
+                                float* __restrict__ grad) {
+    const long long n = (long long)G.nx * G.ny * G.nz;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int x = (int)(i % G.nx);
+        const int y = (int)((i / G.nx) % G.ny);
+        const int z = (int)(i / ((long long)G.nx * G.ny));
+        int x0, x1, y0, y1, z0, z1;
+        fold_range(x, G.nx, G.nb, G.NX, x0, x1);
+        fold_range(y, G.ny, G.nb, G.NY, y0, y1);
+        fold_range(z, G.nz, G.nb, G.NZ, z0, z1);
+        double s = 0.0;
+        for (int zz = z0; zz <= z1; zz++)
+            for (int yy = y0; yy <= y1; yy++)
+                for (int xx = x0; xx <= x1; xx++) {
+                    const long long p = ((long long)zz * G.NY + yy) * G.NX + xx;
+                    s += (double)acc[p] / (double)c[p];
+                }
+        grad[i] = (float)(s * dx3 * dt2);
+    }
+}
+
+__global__ void k_misfit(const float* __restrict__ d, const float* __restrict__ obs, long long n,
+                         float* resid, double* J) {
+    double local = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float r = d[i] - obs[i];
+        if (resid) resid[i] = r;
+        local += 0.5 * (double)r * (double)r;
+    }
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    __shared__ double warp_sum[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_sum[wid] = local;
+    __syncthreads();
+    if (wid == 0) {
+        double v = lane < (int)(blockDim.x >> 5) ? warp_sum[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) atomicAdd(J, v);
+    }
+}
+
+int grid_for(long long n, int block) {
+    long long g = (n + block - 1) / block;
+    if (g > 152 * 16) g = 152 * 16;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_sponge(const Geometry& G, float* gx, float* gy, float* gz, cudaStream_t s) {
+    const int n = max(G.NX, max(G.NY, G.NZ));
+    k_sponge<<<(n + 255) / 256, 256, 0, s>>>(G, gx, gy, gz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wavelet(int nt, double dt, double f0, double t0, float* w, cudaStream_t s) {
+    k_wavelet<<<(nt + 255) / 256, 256, 0, s>>>(nt, dt, f0, t0, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_model_prep(const Geometry& G, const float* vel, int squared, double dt,
+                              float* c, unsigned int* vmax_bits, int* bad, cudaStream_t s) {
+    const long long N = (long long)G.NX * G.NY * G.NZ;
+    k_model_prep<<<grid_for(N, 256), 256, 0, s>>>(G, vel, squared, (float)(dt * dt), c,
+                                                  vmax_bits, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_aux(const Geometry& G, const float* u_cur, float* u_prev, const float* c,
+                           const float* gx, const float* gy, const float* gz,
+                           const int32_t* rec, int nrec, float* data_row, long long src,
+                           const float* w_n, float inv_dx3, int* status, cudaStream_t s) {
+    const int n = nrec + 1;
+    k_fwd_aux<<<(n + 255) / 256, 256, 0, s>>>(G, u_cur, u_prev, c, gx, gy, gz, rec, nrec,
+                                              data_row, src, w_n, inv_dx3, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_aux(const Geometry& G, const float* mu_cur, float* mu_prev,
+                           const float* c, const float* gx, const float* gy, const float* gz,
+                           const int32_t* rec, int nrec, const float* r_row, long long src,
+                           float* src_adj_slot, float* grad_acc, const float* w_n,
+                           float inv_dx3, int* status, cudaStream_t s) {
+    const int n = nrec + 1;
+    k_bwd_aux<<<(n + 255) / 256, 256, 0, s>>>(G, mu_cur, mu_prev, c, gx, gy, gz, rec, nrec,
+                                              r_row, src, src_adj_slot, grad_acc, w_n,
+                                              inv_dx3, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_image_finalize(const Geometry& G, const float* slab, float* image,
+                                  cudaStream_t s) {
+    const long long n = (long long)G.nx * G.ny * G.nz;
+    k_image_finalize<<<grid_for(n, 256), 256, 0, s>>>(G, slab, image);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_finalize(const Geometry& G, const float* acc, const float* c,
+                                 double dx3, double dt2, float* grad_v2, cudaStream_t s) {
+    const long long n = (long long)G.nx * G.ny * G.nz;
+    k_grad_finalize<<<grid_for(n, 256), 256, 0, s>>>(G, acc, c, dx3, dt2, grad_v2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_misfit(const float* d, const float* obs, long long n, float* resid, double* J,
+                          cudaStream_t s) {
+    k_misfit<<<grid_for(n, 256), 256, 0, s>>>(d, obs, n, resid, J);
+    return cudaGetLastError();
+}
+
+}  // namespace rtm

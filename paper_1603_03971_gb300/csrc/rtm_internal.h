@@ -1,0 +1,78 @@
+// Internal declarations shared by the translation units of librtm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace rtm {
+
+// Stencil kernel modes. All of them compute the same leapfrog update
+//   out = g (2 u + c L u) - g^2 prev
+// and differ only in what they do besides.
+enum StencilMode : int {
+    MODE_FWD = 0,       // plain step (forward, or backward without imaging)
+    MODE_FWD_SNAP = 1,  // + write the new field on the model slab (imaging snapshot)
+    MODE_BWD_IMAGE = 2, // + image slab += snapshot * new field
+    MODE_FWD_LU = 3,    // + write L u on the padded grid (gradient snapshot)
+    MODE_BWD_GRAD = 4,  // + grad += new field * snapshot (L u), padded grid
+    MODE_COUNT = 5
+};
+
+constexpr int kMaxRadius = 8;
+
+// Arguments of one stencil launch. The "slab" layout used by imaging
+// snapshots and the internal image is [nz][ny][NX]: z and y restricted to the
+// model region, x over the full padded row, so that it shares the 16-byte
+// alignment of the padded fields.
+struct StepArgs {
+    const float* u_cur;  // u^n (read only)
+    float* u_prev;       // in: u^{n-1}; out: u^{n+1} (updated in place)
+    const float* c;      // v^2 dt^2
+    const float* gx;     // sponge profiles
+    const float* gy;
+    const float* gz;
+    float* snap;         // snapshot (mode dependent)
+    float* acc;          // image slab or gradient accumulator
+    int NX, NY, NZ;      // padded grid
+    int nb, nx, ny, nz;  // model region
+    int zchunk;          // z planes per thread block
+    float a[kMaxRadius + 1];  // a[0] = 3 a0 / dx^2, a[k] = a_k / dx^2
+};
+
+cudaError_t launch_stencil(int radius, int mode, const StepArgs& a, cudaStream_t s);
+int auto_zchunk(int radius, int NX, int NY, int NZ);
+
+// ---- small kernels (aux.cu) -------------------------------------------------
+struct Geometry {
+    int NX, NY, NZ, nb, nx, ny, nz;
+};
+
+cudaError_t launch_sponge(const Geometry& G, float* gx, float* gy, float* gz, cudaStream_t s);
+cudaError_t launch_wavelet(int nt, double dt, double f0, double t0, float* w, cudaStream_t s);
+cudaError_t launch_model_prep(const Geometry& G, const float* vel, int squared, double dt,
+                              float* c, unsigned int* vmax_bits, int* bad, cudaStream_t s);
+// forward step n: gather d[n-1] = u_cur[rec] (if data_row), then pre-adjust
+// u_prev[s] -= c_s w / (dx^3 g_s^2) so that the stencil adds c_s w / dx^3.
+cudaError_t launch_fwd_aux(const Geometry& G, const float* u_cur, float* u_prev,
+                           const float* c, const float* gx, const float* gy,
+                           const float* gz, const int32_t* rec, int nrec,
+                           float* data_row, long long src, const float* w_n,
+                           float inv_dx3, int* status, cudaStream_t s);
+// backward step m: pre-adjust mu_prev[rec] -= c r / (dx^3 g) (if r_row) so
+// that the stencil adds c g r / dx^3; record the source trace of mu_cur and
+// the source term of the gradient (if requested).
+cudaError_t launch_bwd_aux(const Geometry& G, const float* mu_cur, float* mu_prev,
+                           const float* c, const float* gx, const float* gy,
+                           const float* gz, const int32_t* rec, int nrec,
+                           const float* r_row, long long src, float* src_adj_slot,
+                           float* grad_acc, const float* w_n, float inv_dx3,
+                           int* status, cudaStream_t s);
+cudaError_t launch_image_finalize(const Geometry& G, const float* slab, float* image,
+                                  cudaStream_t s);
+cudaError_t launch_grad_finalize(const Geometry& G, const float* acc, const float* c,
+                                 double dx3, double dt2, float* grad_v2, cudaStream_t s);
+cudaError_t launch_misfit(const float* d, const float* obs, long long n, float* resid,
+                          double* J, cudaStream_t s);
+
+}  // namespace rtm
