@@ -190,6 +190,39 @@ rtm_status rtm_shot_host(const rtm_params *p, const float *h_vel, int32_t vel_ki
  * RTM_ERR_TIMEOUT (a bounded wait ran out) or RTM_ERR_CUDA. */
 rtm_status rtm_check(void *d_ws, size_t ws_bytes, rtm_stream stream);
 
+/* Size of the static device scratch of rtm_forward_noalloc: 24 MiB. */
+#define RTM_NOALLOC_SCRATCH_BYTES (24u << 20)
+
+/* Forward modelling without any device allocation and without a workspace.
+ * (The paper has no counterpart; this is a deployment convenience.)
+ *
+ * For callers that cannot call cudaMalloc or hand out a workspace: code that
+ * runs inside a host application owning every device allocation, plugins that
+ * may not touch the process's allocator, or callers that must keep the
+ * device's memory footprint fixed. They pass only the inputs and outputs,
+ * exactly as for rtm_forward (d_c, d_rec, d_data [nt][nrec] or NULL,
+ * d_u_last [2][NZ][NY][NX] or NULL).
+ *
+ * The scratch (the two wavefields, the wavelet, the sponge profiles and a
+ * status word) is a file-scope static device array of
+ * RTM_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
+ * the process exits. Problems whose two padded fields plus tables do not fit
+ * (about 2.9 M padded points, e.g. 104^3 fits) are rejected with
+ * RTM_ERR_WORKSPACE and a message naming the sizes; nothing is allocated,
+ * freed or copied to host memory by this call.
+ *
+ * The first call on each device looks the scratch's device address up
+ * (cudaGetSymbolAddress with that device current); make that first call
+ * before capturing the stream into a CUDA graph. All calls share the one
+ * array, which keeps the previous call's contents: each call clears what must
+ * start at zero. Calls whose execution overlaps on the GPU (other streams or
+ * threads) race on the array and must be serialised by the caller. It stores
+ * no snapshots or checkpoints, so it cannot feed rtm_backward_image; receivers
+ * outside the padded grid get zero traces and are not reported (there is no
+ * workspace for rtm_check). It does not update rtm_stats. */
+rtm_status rtm_forward_noalloc(const rtm_params *p, const float *d_c, const int32_t *d_rec,
+                               float *d_data, float *d_u_last, rtm_stream stream);
+
 /* Stencil tuning: z extent of the slab one thread block marches through
  * (0 = automatic) and the plane-load path (0 = automatic, 1 = vector loads
  * through registers, 2 = TMA). Applies to later calls on every thread. */

@@ -78,6 +78,7 @@ SIGNATURES = {
     "rtm_host_workspace_size": (_sz, [_P]),
     "rtm_shot_host": (ctypes.c_int, [_P, _vp, _i32, _vp, _vp, _vp, _vp, _sz, _vp]),
     "rtm_check": (ctypes.c_int, [_vp, _sz, _vp]),
+    "rtm_forward_noalloc": (ctypes.c_int, [_P, _vp, _vp, _vp, _vp, _vp]),
     "rtm_set_tuning": (ctypes.c_int, [_i32, _i32, _i32]),
     "rtm_set_timing": (ctypes.c_int, [_i32]),
     "rtm_stats_get": (ctypes.c_int, [ctypes.POINTER(RtmStats)]),

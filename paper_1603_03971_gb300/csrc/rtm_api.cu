@@ -506,6 +506,16 @@ rtm_status common_checks(const rtm_params* p, const float* d_c, const int32_t* d
 
 }  // namespace
 
+int rtm::set_error(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
 // ==== C ABI ======================================================================
 extern "C" {
 

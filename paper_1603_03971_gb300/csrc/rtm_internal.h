@@ -75,4 +75,7 @@ cudaError_t launch_grad_finalize(const Geometry& G, const float* acc, const floa
 cudaError_t launch_misfit(const float* d, const float* obs, long long n, float* resid,
                           double* J, cudaStream_t s);
 
+// sets the thread-local message of rtm_last_error() and returns code
+int set_error(int code, const char* fmt, ...);
+
 }  // namespace rtm
