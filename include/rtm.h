@@ -67,7 +67,7 @@ typedef enum {
     RTM_ERR_STATE = 8        /* workspace prepared for another purpose */
 } rtm_status;
 
-enum { RTM_STORE_ALL = 0, RTM_STORE_CKPT = 1 };
+enum { RTM_STORE_ALL = 0, RTM_STORE_CKPT = 1, RTM_STORE_LEARNED = 2 };
 enum { RTM_VEL_V = 0, RTM_VEL_V2 = 1 };
 
 typedef struct {
@@ -82,7 +82,9 @@ typedef struct {
     int32_t src_x, src_y, src_z; /* source, model coordinates in [-nb, n + nb) */
     int32_t nrec;           /* receivers */
     int32_t storage;        /* RTM_STORE_ALL: keep every imaging snapshot;
-                               RTM_STORE_CKPT: checkpoints + segment recompute */
+                               RTM_STORE_CKPT: checkpoints + segment recompute;
+                               RTM_STORE_LEARNED: an 8x autoencoder latent per
+                               imaging snapshot (the *_learned calls) */
     int32_t ckpt_every;     /* steps per checkpoint segment (RTM_STORE_CKPT) */
     int32_t image_every;    /* image at steps m with m % image_every == 0 (>= 1) */
     int32_t want_grad;      /* 1: prepare the workspace for rtm_grad instead of imaging */
@@ -167,6 +169,28 @@ rtm_status rtm_grad(const rtm_params *p, const float *d_c, const int32_t *d_rec,
                     const float *d_resid, void *d_ws, size_t ws_bytes, float *d_grad_v2,
                     rtm_stream stream);
 
+/* Learned storage (p->storage == RTM_STORE_LEARNED, model sides multiples of
+ * 4): the forward pass encodes each imaging snapshot u^m (m % image_every ==
+ * 0) into a bfloat16 latent in the workspace right after the stencil writes
+ * it; the backward pass decodes it just before the backward stencil that
+ * images with it. No checkpoints, no recompute. d_ae_params: the codec's
+ * RTM_AE_NPARAMS float32 parameters (see rtm_ae_encode). Otherwise as
+ * rtm_forward / rtm_backward_image / rtm_shot. */
+rtm_status rtm_forward_learned(const rtm_params *p, const float *d_c, const int32_t *d_rec,
+                               float *d_data, const float *d_ae_params, void *d_ws,
+                               size_t ws_bytes, rtm_stream stream);
+rtm_status rtm_backward_image_learned(const rtm_params *p, const float *d_c, const int32_t *d_rec,
+                                      const float *d_rdata, const float *d_ae_params, void *d_ws,
+                                      size_t ws_bytes, float *d_image, rtm_stream stream);
+rtm_status rtm_shot_learned(const rtm_params *p, const float *d_c, const int32_t *d_rec,
+                            const float *d_dobs, const float *d_ae_params, void *d_ws,
+                            size_t ws_bytes, float *d_image, rtm_stream stream);
+
+/* Copy the stored imaging snapshot u^m (m a multiple of image_every) of a
+ * store-all imaging workspace, after rtm_forward, into d_out [nz][ny][nx]. */
+rtm_status rtm_snapshot(const rtm_params *p, const void *d_ws, size_t ws_bytes, int32_t m,
+                        float *d_out, rtm_stream stream);
+
 /* Misfit: d_resid[i] = d_data[i] - d_obs[i]; *d_J = 1/2 sum d_resid^2
  * accumulated in float64 (overwritten). d_resid may be NULL. */
 rtm_status rtm_misfit(const float *d_data, const float *d_obs, int64_t n, float *d_resid,
@@ -189,6 +213,52 @@ rtm_status rtm_shot_host(const rtm_params *p, const float *h_vel, int32_t vel_ki
  * workspace: RTM_OK, RTM_ERR_INVALID (a receiver out of range was skipped),
  * RTM_ERR_TIMEOUT (a bounded wait ran out) or RTM_ERR_CUDA. */
 rtm_status rtm_check(void *d_ws, size_t ws_bytes, rtm_stream stream);
+
+/* ---- learned snapshot compression (tensor cores) ------------------------
+ * A 4-layer 3D convolutional autoencoder compresses a float32 snapshot
+ * [nz][ny][nx] (every side a multiple of 4) 8x, into a bfloat16 latent
+ * [nz/4][ny/4][nx/4][16] plus one float32 scale (the snapshot's rms):
+ *   x0 = s / rms(s); h1 = LeakyReLU(conv 1->32, kernel 2, stride 2);
+ *   latent = conv 32->16 (kernel 3, stride 2, padding 1);
+ *   g1 = LeakyReLU(transposed conv 16->32, kernel 4, stride 2, padding 1);
+ *   s_hat = rms(s) * transposed conv 32->1 (kernel 2, stride 2).
+ * Every convolution (forward, data gradient, weight gradient) runs as an
+ * implicit GEMM on tcgen05 tensor cores (bfloat16 operands, float32
+ * accumulation in tensor memory). The paper has no learned part; the codec
+ * stands in for the recompute of the source wavefield in the imaging
+ * condition. Parameters: RTM_AE_NPARAMS float32 in the order W1[32][2][2][2],
+ * b1[32], W2[16][3][3][3][32], b2[16], W3[32][4][4][4][16], b3[32],
+ * W4[2][2][2][32], b4[1]. Strides sy, sz are in elements (x contiguous). */
+#define RTM_AE_NPARAMS 47185
+size_t rtm_ae_param_count(void);
+/* Workspace bytes for the codec calls on an nx * ny * nz volume (0 if a side
+ * is not a positive multiple of 4). Its first word is a status word that
+ * rtm_check reads. */
+size_t rtm_ae_workspace_size(int32_t nx, int32_t ny, int32_t nz);
+/* d_latent [nz/4][ny/4][nx/4][16] bfloat16 out; d_scale [1] out (may be NULL). */
+rtm_status rtm_ae_encode(const float *d_params, const float *d_snap, int64_t sy, int64_t sz,
+                         int32_t nx, int32_t ny, int32_t nz, uint16_t *d_latent, float *d_scale,
+                         void *d_ws, size_t ws_bytes, rtm_stream stream);
+/* d_out [nz][ny][nx] (strided) out = scale * decoder(latent); d_scale may be
+ * NULL (scale 1). */
+rtm_status rtm_ae_decode(const float *d_params, const uint16_t *d_latent, const float *d_scale,
+                         float *d_out, int64_t sy, int64_t sz, int32_t nx, int32_t ny,
+                         int32_t nz, void *d_ws, size_t ws_bytes, rtm_stream stream);
+/* One training step on d_batch [batch][nz][ny][nx] (dense): the mean over
+ * the batch of mean((y - x0)^2) in normalised units goes to *d_loss (float64),
+ * its gradient (hand-written backward through every layer, gradient
+ * operands rounded to bfloat16 for the tensor cores) to d_grad if not NULL,
+ * then Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected at step >= 1)
+ * updates d_params in place unless lr <= 0. */
+rtm_status rtm_ae_train_step(float *d_params, float *d_adam_m, float *d_adam_v, int32_t step,
+                             float lr, const float *d_batch, int32_t batch, int32_t nx,
+                             int32_t ny, int32_t nz, double *d_loss, float *d_grad, void *d_ws,
+                             size_t ws_bytes, rtm_stream stream);
+/* The tensor-core engine under the codec, exposed for checking: C[M][N] =
+ * A[M][K] * B[N][K]^T, bfloat16 in, float32 out, K a multiple of 32, N 16 or
+ * 32. A bounded wait that runs out writes RTM_ERR_TIMEOUT to *d_status. */
+rtm_status rtm_ae_gemm_bf16(const uint16_t *d_A, const uint16_t *d_B, float *d_C, int32_t M,
+                            int32_t K, int32_t N, int32_t *d_status, rtm_stream stream);
 
 /* Size of the static device scratch of rtm_forward_noalloc: 24 MiB. */
 #define RTM_NOALLOC_SCRATCH_BYTES (24u << 20)

@@ -16,13 +16,14 @@ from typing import Optional
 
 import torch
 
-from ._lib import (RTM_STORE_ALL, RTM_STORE_CKPT, RTM_VEL_V, RTM_VEL_V2, RtmError,
-                   RtmParams, RtmStats, call, lib)
+from ._lib import (RTM_STORE_ALL, RTM_STORE_CKPT, RTM_STORE_LEARNED, RTM_VEL_V, RTM_VEL_V2,
+                   RtmError, RtmParams, RtmStats, call, lib)
 
 __all__ = [
     "RtmParams", "RtmError", "make_params", "params_for", "padded_shape", "workspace_size",
     "host_workspace_size", "alloc_workspace", "model_prep", "forward", "backward_image",
-    "shot", "grad", "misfit", "check", "shot_host", "set_tuning", "set_timing", "stats",
+    "shot", "grad", "misfit", "check", "shot_host", "forward_learned",
+    "backward_image_learned", "shot_learned", "snapshot", "set_tuning", "set_timing", "stats",
     "reset_stats", "RtmMisfit", "version",
 ]
 
@@ -38,7 +39,8 @@ def make_params(nx, ny, nz, nb, radius, nt, dx, dt, f0, t0, src, nrec, storage="
     p.dx, p.dt, p.f0, p.t0 = float(dx), float(dt), float(f0), float(t0)
     p.src_x, p.src_y, p.src_z = (int(v) for v in src)
     p.nrec = int(nrec)
-    p.storage = RTM_STORE_ALL if storage == "all" else RTM_STORE_CKPT
+    p.storage = {"all": RTM_STORE_ALL, "ckpt": RTM_STORE_CKPT,
+                 "learned": RTM_STORE_LEARNED}[storage]
     p.ckpt_every = int(ckpt_every)
     p.image_every = int(image_every)
     p.want_grad = 1 if want_grad else 0
@@ -147,6 +149,38 @@ def shot(p: RtmParams, c, rec, dobs, ws, image, data=None, stream=None):
          _dev(dobs, name="dobs"), _dev(data, name="data"), w, wb, _dev(image, name="image"),
          _stream(stream))
     return image
+
+
+def forward_learned(p: RtmParams, c, rec, ae_params, ws, data=None, stream=None):
+    w, wb = _ws(ws)
+    call("rtm_forward_learned", ctypes.byref(p), _dev(c, name="c"), _dev(rec, torch.int32, "rec"),
+         _dev(data, name="data"), _dev(ae_params, name="ae_params"), w, wb, _stream(stream))
+    return data
+
+
+def backward_image_learned(p: RtmParams, c, rec, rdata, ae_params, ws, image, stream=None):
+    w, wb = _ws(ws)
+    call("rtm_backward_image_learned", ctypes.byref(p), _dev(c, name="c"),
+         _dev(rec, torch.int32, "rec"), _dev(rdata, name="rdata"),
+         _dev(ae_params, name="ae_params"), w, wb, _dev(image, name="image"), _stream(stream))
+    return image
+
+
+def shot_learned(p: RtmParams, c, rec, dobs, ae_params, ws, image, stream=None):
+    w, wb = _ws(ws)
+    call("rtm_shot_learned", ctypes.byref(p), _dev(c, name="c"), _dev(rec, torch.int32, "rec"),
+         _dev(dobs, name="dobs"), _dev(ae_params, name="ae_params"), w, wb,
+         _dev(image, name="image"), _stream(stream))
+    return image
+
+
+def snapshot(p: RtmParams, ws, m: int, out=None, stream=None):
+    """Stored imaging snapshot u^m of a store-all workspace (model grid)."""
+    if out is None:
+        out = torch.empty(model_shape(p), dtype=torch.float32, device=ws.device)
+    w, wb = _ws(ws)
+    call("rtm_snapshot", ctypes.byref(p), w, wb, int(m), _dev(out, name="out"), _stream(stream))
+    return out
 
 
 def grad(p: RtmParams, c, rec, resid, ws, out=None, stream=None):

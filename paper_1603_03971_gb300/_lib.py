@@ -16,7 +16,7 @@ STATUS_NAMES = {
     4: "RTM_ERR_CUDA", 5: "RTM_ERR_TIMEOUT", 6: "RTM_ERR_NUMERIC", 7: "RTM_ERR_UNSUPPORTED",
     8: "RTM_ERR_STATE",
 }
-RTM_STORE_ALL, RTM_STORE_CKPT = 0, 1
+RTM_STORE_ALL, RTM_STORE_CKPT, RTM_STORE_LEARNED = 0, 1, 2
 RTM_VEL_V, RTM_VEL_V2 = 0, 1
 
 
@@ -80,6 +80,19 @@ SIGNATURES = {
     "rtm_check": (ctypes.c_int, [_vp, _sz, _vp]),
     "rtm_forward_noalloc": (ctypes.c_int, [_P, _vp, _vp, _vp, _vp, _vp]),
     "rtm_set_tuning": (ctypes.c_int, [_i32, _i32, _i32]),
+    "rtm_forward_learned": (ctypes.c_int, [_P, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "rtm_backward_image_learned": (ctypes.c_int, [_P, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _vp]),
+    "rtm_shot_learned": (ctypes.c_int, [_P, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _vp]),
+    "rtm_snapshot": (ctypes.c_int, [_P, _vp, _sz, _i32, _vp, _vp]),
+    "rtm_ae_param_count": (_sz, []),
+    "rtm_ae_workspace_size": (_sz, [_i32, _i32, _i32]),
+    "rtm_ae_encode": (ctypes.c_int, [_vp, _vp, _i64, _i64, _i32, _i32, _i32, _vp, _vp, _vp, _sz,
+                                     _vp]),
+    "rtm_ae_decode": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _i64, _i32, _i32, _i32, _vp, _sz,
+                                     _vp]),
+    "rtm_ae_train_step": (ctypes.c_int, [_vp, _vp, _vp, _i32, ctypes.c_float, _vp, _i32, _i32,
+                                         _i32, _i32, _vp, _vp, _vp, _sz, _vp]),
+    "rtm_ae_gemm_bf16": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     "rtm_set_timing": (ctypes.c_int, [_i32]),
     "rtm_stats_get": (ctypes.c_int, [ctypes.POINTER(RtmStats)]),
     "rtm_stats_reset": (ctypes.c_int, []),

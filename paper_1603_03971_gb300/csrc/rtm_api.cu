@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/rtm.h"
+#include "ae_internal.h"
 #include "rtm_internal.h"
 
 using namespace rtm;
@@ -131,6 +132,8 @@ struct Layout {
     size_t img = 0, grad = 0;
     size_t ckpt = 0, nckpt = 0;
     size_t snap = 0, nsnap = 0, snap_elems = 0;
+    // learned storage: one latent and one scale per imaging step, codec scratch
+    size_t latent = 0, latent_bytes = 0, scales = 0, ae_h = 0, ae_scalars = 0;
     size_t total = 0;
 };
 
@@ -176,7 +179,15 @@ Layout layout_of(const rtm_params* p) {
         L.img = take(sizeof(float) * d.slab);
         L.snap_elems = d.slab;
     }
-    if (p->storage == RTM_STORE_ALL) {
+    if (p->storage == RTM_STORE_LEARNED) {
+        const size_t nlat = (size_t)(p->nt / p->image_every);
+        L.latent_bytes = up((size_t)(p->nx / 4) * (p->ny / 4) * (p->nz / 4) * 16 * 2);
+        L.latent = take(L.latent_bytes * (nlat ? nlat : 1));
+        L.scales = take(sizeof(float) * (nlat ? nlat : 1));
+        L.ae_h = take((size_t)(p->nx / 2) * (p->ny / 2) * (p->nz / 2) * 32 * 2);
+        L.ae_scalars = take(256);
+        L.nsnap = 1;  // one snapshot slab, encoded or decoded in place
+    } else if (p->storage == RTM_STORE_ALL) {
         L.nsnap = p->want_grad ? (size_t)p->nt : (size_t)(p->nt / p->image_every);
     } else {
         const int k = p->ckpt_every;
@@ -215,8 +226,15 @@ rtm_status validate(const rtm_params* p) {
         return fail(RTM_ERR_INVALID, "source (%d,%d,%d) outside the padded grid", p->src_x,
                     p->src_y, p->src_z);
     if (p->nrec < 0) return fail(RTM_ERR_INVALID, "nrec %d < 0", p->nrec);
-    if (p->storage != RTM_STORE_ALL && p->storage != RTM_STORE_CKPT)
+    if (p->storage != RTM_STORE_ALL && p->storage != RTM_STORE_CKPT &&
+        p->storage != RTM_STORE_LEARNED)
         return fail(RTM_ERR_INVALID, "storage %d unknown", p->storage);
+    if (p->storage == RTM_STORE_LEARNED) {
+        if (p->nx % 4 || p->ny % 4 || p->nz % 4)
+            return fail(RTM_ERR_INVALID, "learned storage needs model sides that are multiples of 4");
+        if (p->want_grad)
+            return fail(RTM_ERR_INVALID, "learned storage serves imaging, not the gradient");
+    }
     if (p->storage == RTM_STORE_CKPT && p->ckpt_every < 1)
         return fail(RTM_ERR_INVALID, "ckpt_every %d < 1", p->ckpt_every);
     if (p->image_every < 1) return fail(RTM_ERR_INVALID, "image_every %d < 1", p->image_every);
@@ -250,8 +268,15 @@ struct Ctx {
     long long src;
     float inv_dx3;
     int variant;
+    const float* ae = nullptr;  // codec parameters (learned storage)
 
     float* at(size_t off) const { return reinterpret_cast<float*>(ws + off); }
+    ae::bf16* latent_slot(size_t k) const {
+        return reinterpret_cast<ae::bf16*>(ws + L.latent + k * L.latent_bytes);
+    }
+    ae::Vol model_view(float* slab) const {
+        return ae::Vol{slab + p->nb, (long long)d.NX, (long long)d.NX * p->ny, p->nx, p->ny, p->nz};
+    }
     int* status() const { return reinterpret_cast<int*>(ws + L.status); }
     float* wav() const { return at(L.wavelet); }
     float* snap_slot(size_t k) const { return at(L.snap) + k * L.snap_elems; }
@@ -392,8 +417,18 @@ rtm_status run_forward(Ctx& C, const int32_t* rec, float* data, float* u_last) {
                 mode = MODE_FWD_SNAP;
                 snap = C.snap_slot((size_t)((n + 1) / ie - 1));
             }
+        } else if (p->storage == RTM_STORE_LEARNED && (n + 1) % ie == 0) {
+            mode = MODE_FWD_SNAP;
+            snap = C.snap_slot(0);
         }
         CHECK(stencil(C, mode, cur, prev, snap, nullptr));
+        if (p->storage == RTM_STORE_LEARNED && (n + 1) % ie == 0) {
+            const size_t k = (size_t)((n + 1) / ie - 1);
+            CU(ae_encode(C.ae, C.model_view(snap), reinterpret_cast<ae::bf16*>(C.at(C.L.ae_h)),
+                         C.latent_slot(k), reinterpret_cast<ae::AeScalars*>(C.at(C.L.ae_scalars)),
+                         C.at(C.L.scales) + k, C.status(), C.s));
+            count_launch(4);
+        }
         float* t = prev;
         prev = cur;
         cur = t;
@@ -437,7 +472,20 @@ rtm_status run_backward(Ctx& C, const int32_t* rec, const float* rdata, float* s
         return RTM_OK;
     };
 
-    if (p->storage == RTM_STORE_ALL) {
+    if (p->storage == RTM_STORE_LEARNED) {
+        float* slab = C.snap_slot(0);
+        // columns outside the model stay finite (the decoder writes model columns)
+        CU(cudaMemsetAsync(slab, 0, sizeof(float) * C.d.slab, C.s));
+        for (int m = p->nt; m >= 1; m--) {
+            if (m % ie == 0) {
+                const size_t k = (size_t)(m / ie - 1);
+                CU(ae_decode(C.ae, C.latent_slot(k), C.at(C.L.scales) + k, C.model_view(slab),
+                             reinterpret_cast<ae::bf16*>(C.at(C.L.ae_h)), C.status(), C.s));
+                count_launch(2);
+            }
+            CHECK(back_step(m, slab));
+        }
+    } else if (p->storage == RTM_STORE_ALL) {
         for (int m = p->nt; m >= 1; m--) {
             float* snap = nullptr;
             if (grad) snap = C.snap_slot((size_t)(m - 1));
@@ -570,6 +618,8 @@ rtm_status rtm_model_prep(const rtm_params* p, const float* d_vel, int32_t vel_k
 rtm_status rtm_forward(const rtm_params* p, const float* d_c, const int32_t* d_rec, float* d_data,
                        void* d_ws, size_t ws_bytes, float* d_u_last, rtm_stream stream) {
     CHECK(common_checks(p, d_c, d_rec, d_ws, ws_bytes));
+    if (p->storage == RTM_STORE_LEARNED)
+        return fail(RTM_ERR_STATE, "learned storage: use rtm_forward_learned");
     Ctx C;
     CHECK(make_ctx(C, p, d_c, d_ws, stream));
     CHECK(run_forward(C, d_rec, d_data, d_u_last));
@@ -582,6 +632,8 @@ rtm_status rtm_backward_image(const rtm_params* p, const float* d_c, const int32
     CHECK(common_checks(p, d_c, d_rec, d_ws, ws_bytes));
     if (p->want_grad)
         return fail(RTM_ERR_STATE, "workspace prepared for the gradient (want_grad = 1)");
+    if (p->storage == RTM_STORE_LEARNED)
+        return fail(RTM_ERR_STATE, "learned storage: use rtm_backward_image_learned");
     if (!d_rdata && p->nrec > 0) return fail(RTM_ERR_INVALID, "receiver data is NULL");
     if (!d_image) return fail(RTM_ERR_INVALID, "image is NULL");
     Ctx C;
@@ -598,6 +650,8 @@ rtm_status rtm_shot(const rtm_params* p, const float* d_c, const int32_t* d_rec,
     CHECK(common_checks(p, d_c, d_rec, d_ws, ws_bytes));
     if (p->want_grad)
         return fail(RTM_ERR_STATE, "workspace prepared for the gradient (want_grad = 1)");
+    if (p->storage == RTM_STORE_LEARNED)
+        return fail(RTM_ERR_STATE, "learned storage: use rtm_shot_learned");
     if (!d_dobs && p->nrec > 0) return fail(RTM_ERR_INVALID, "observed data is NULL");
     if (!d_image) return fail(RTM_ERR_INVALID, "image is NULL");
     Ctx C;
@@ -624,6 +678,77 @@ rtm_status rtm_grad(const rtm_params* p, const float* d_c, const int32_t* d_rec,
                             d_grad_v2, C.s));
     count_launch();
     return finish(C);
+}
+
+static rtm_status learned_checks(const rtm_params* p, const float* d_c, const int32_t* d_rec,
+                                 const float* d_ae, void* d_ws, size_t ws_bytes) {
+    CHECK(common_checks(p, d_c, d_rec, d_ws, ws_bytes));
+    if (p->storage != RTM_STORE_LEARNED)
+        return fail(RTM_ERR_STATE, "the learned calls need storage = RTM_STORE_LEARNED");
+    if (!d_ae) return fail(RTM_ERR_INVALID, "codec parameters are NULL");
+    return RTM_OK;
+}
+
+rtm_status rtm_forward_learned(const rtm_params* p, const float* d_c, const int32_t* d_rec,
+                               float* d_data, const float* d_ae_params, void* d_ws,
+                               size_t ws_bytes, rtm_stream stream) {
+    CHECK(learned_checks(p, d_c, d_rec, d_ae_params, d_ws, ws_bytes));
+    Ctx C;
+    CHECK(make_ctx(C, p, d_c, d_ws, stream));
+    C.ae = d_ae_params;
+    CHECK(run_forward(C, d_rec, d_data, nullptr));
+    return finish(C);
+}
+
+rtm_status rtm_backward_image_learned(const rtm_params* p, const float* d_c, const int32_t* d_rec,
+                                      const float* d_rdata, const float* d_ae_params, void* d_ws,
+                                      size_t ws_bytes, float* d_image, rtm_stream stream) {
+    CHECK(learned_checks(p, d_c, d_rec, d_ae_params, d_ws, ws_bytes));
+    if (!d_rdata && p->nrec > 0) return fail(RTM_ERR_INVALID, "receiver data is NULL");
+    if (!d_image) return fail(RTM_ERR_INVALID, "image is NULL");
+    Ctx C;
+    CHECK(make_ctx(C, p, d_c, d_ws, stream));
+    C.ae = d_ae_params;
+    CHECK(run_backward(C, d_rec, d_rdata, nullptr, false));
+    CU(launch_image_finalize(C.G, C.at(C.L.img), d_image, C.s));
+    count_launch();
+    return finish(C);
+}
+
+rtm_status rtm_shot_learned(const rtm_params* p, const float* d_c, const int32_t* d_rec,
+                            const float* d_dobs, const float* d_ae_params, void* d_ws,
+                            size_t ws_bytes, float* d_image, rtm_stream stream) {
+    CHECK(learned_checks(p, d_c, d_rec, d_ae_params, d_ws, ws_bytes));
+    if (!d_dobs && p->nrec > 0) return fail(RTM_ERR_INVALID, "observed data is NULL");
+    if (!d_image) return fail(RTM_ERR_INVALID, "image is NULL");
+    Ctx C;
+    CHECK(make_ctx(C, p, d_c, d_ws, stream));
+    C.ae = d_ae_params;
+    CHECK(run_forward(C, d_rec, nullptr, nullptr));
+    CHECK(run_backward(C, d_rec, d_dobs, nullptr, false));
+    CU(launch_image_finalize(C.G, C.at(C.L.img), d_image, C.s));
+    count_launch();
+    return finish(C);
+}
+
+rtm_status rtm_snapshot(const rtm_params* p, const void* d_ws, size_t ws_bytes, int32_t m,
+                        float* d_out, rtm_stream stream) {
+    CHECK(validate(p));
+    CHECK(check_ws(p, const_cast<void*>(d_ws), ws_bytes));
+    if (p->storage != RTM_STORE_ALL || p->want_grad)
+        return fail(RTM_ERR_STATE, "snapshots are kept only by store-all imaging workspaces");
+    if (m < p->image_every || m > p->nt || m % p->image_every)
+        return fail(RTM_ERR_INVALID, "no stored snapshot for step %d", m);
+    if (!d_out) return fail(RTM_ERR_INVALID, "output is NULL");
+    const Dims d = dims_of(p);
+    const Layout L = layout_of(p);
+    const char* base = reinterpret_cast<const char*>(d_ws) + L.snap +
+                       sizeof(float) * L.snap_elems * (size_t)(m / p->image_every - 1);
+    const float* src = reinterpret_cast<const float*>(base) + p->nb;
+    CU(cudaMemcpy2DAsync(d_out, sizeof(float) * p->nx, src, sizeof(float) * d.NX,
+                         sizeof(float) * p->nx, (size_t)p->nz * p->ny, cudaMemcpyDeviceToDevice,
+                         reinterpret_cast<cudaStream_t>(stream)));
+    return RTM_OK;
 }
 
 rtm_status rtm_misfit(const float* d_data, const float* d_obs, int64_t n, float* d_resid,

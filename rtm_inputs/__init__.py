@@ -318,3 +318,32 @@ WORKLOADS = {
 # 16th-order stencil, 1500 steps each
 BATCH_WORKLOAD = dict(model_shape=(512, 1024, 1024), nshots=32, radius=8, nt=1500,
                       f0=20.0, dx=10.0, nb=32, vmax=4500.0, seed=4)
+
+
+# ----------------------------------------------------------------------------
+# seeded initial weights of the snapshot-compression autoencoder
+# ----------------------------------------------------------------------------
+
+AE_SHAPES = (("W1", (32, 2, 2, 2), 8, 1.0), ("b1", (32,), 0, 0.0),
+             ("W2", (16, 3, 3, 3, 32), 27 * 32, 0.5), ("b2", (16,), 0, 0.0),
+             ("W3", (32, 4, 4, 4, 16), 8 * 16, 1.0), ("b3", (32,), 0, 0.0),
+             ("W4", (2, 2, 2, 32), 32, 0.5), ("b4", (1,), 0, 0.0))
+
+
+def ae_init_params(seed: int = 0):
+    """Seeded initial autoencoder parameters (He-style: N(0,1) * gain *
+    sqrt(2 / fan_in); biases zero), as a dict of float64 arrays in the order
+    W1 b1 W2 b2 W3 b3 W4 b4."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = {}
+    for name, shape, fan_in, gain in AE_SHAPES:
+        if fan_in:
+            out[name] = rng.standard_normal(shape) * math.sqrt(2.0 / fan_in) * gain
+        else:
+            out[name] = np.zeros(shape)
+    return out
+
+
+def ae_flat(params) -> np.ndarray:
+    """Flat float64 vector of autoencoder parameters in the order of AE_SHAPES."""
+    return np.concatenate([np.asarray(params[n], np.float64).ravel() for n, *_ in AE_SHAPES])
