@@ -248,8 +248,9 @@ rtm_status rtm_ae_decode(const float *d_params, const uint16_t *d_latent, const 
  * the batch of mean((y - x0)^2) in normalised units goes to *d_loss (float64),
  * its gradient (hand-written backward through every layer, gradient
  * operands rounded to bfloat16 for the tensor cores) to d_grad if not NULL,
- * then Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected at step >= 1)
- * updates d_params in place unless lr <= 0. */
+ * then Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected at step >= 1,
+ * gradient scaled to a global L2 norm of at most 1) updates d_params in
+ * place unless lr <= 0. */
 rtm_status rtm_ae_train_step(float *d_params, float *d_adam_m, float *d_adam_v, int32_t step,
                              float lr, const float *d_batch, int32_t batch, int32_t nx,
                              int32_t ny, int32_t nz, double *d_loss, float *d_grad, void *d_ws,
@@ -259,6 +260,39 @@ rtm_status rtm_ae_train_step(float *d_params, float *d_adam_m, float *d_adam_v, 
  * 32. A bounded wait that runs out writes RTM_ERR_TIMEOUT to *d_status. */
 rtm_status rtm_ae_gemm_bf16(const uint16_t *d_A, const uint16_t *d_B, float *d_C, int32_t M,
                             int32_t K, int32_t N, int32_t *d_status, rtm_stream stream);
+
+/* ---- batched shots on uneven apertures (one persistent launch per wave) ----
+ * Each shot runs a full RTM (forward modelling with checkpoints every
+ * p->ckpt_every steps, segment recompute, receiver propagation with zero-lag
+ * imaging every p->image_every steps) on its own aperture of a common model,
+ * padded by p->nb sponge cells, receivers at every (x, y) of the aperture at
+ * depth rec_z. All shots of a wave run inside ONE cooperative persistent
+ * kernel launch: blocks take (phase step, shot, tile) work items from an
+ * atomic queue and wait (bounded) for the previous phase step of the same
+ * shot, so uneven apertures balance dynamically. Waves are consecutive shots
+ * whose buffers fit budget_bytes (0: one wave); the call captures every
+ * wave's model preparation, persistent launch and image stack into one CUDA
+ * graph, launches it and synchronises the stream.
+ *   p: nx, ny, nz = the full model; radius, nb, nt, dx, dt, f0, t0,
+ *      ckpt_every, image_every as for one shot; storage = RTM_STORE_CKPT.
+ *   d_vel   [nz][ny][nx] velocity of the full model (m/s).
+ *   d_dobs  per-shot data [nt][ny_s][nx_s], concatenated in shot order.
+ *   d_data  modelled data in the same layout, or NULL.
+ *   d_image [nz][ny][nx] of the full model, ACCUMULATED: each shot adds its
+ *           image at its aperture, in shot order (deterministic).
+ *   zchunk  z planes per work item (0: automatic). */
+typedef struct {
+    int32_t ox, oy, oz;          /* aperture origin in the full model */
+    int32_t nx, ny, nz;          /* aperture size */
+    int32_t src_x, src_y, src_z; /* source, aperture coordinates */
+    int32_t rec_z;               /* receiver plane depth, aperture coordinates */
+} rtm_aperture;
+size_t rtm_batch_workspace_size(const rtm_params *p, int32_t nshots, const rtm_aperture *h_shots,
+                                size_t budget_bytes);
+rtm_status rtm_batch(const rtm_params *p, int32_t nshots, const rtm_aperture *h_shots,
+                     const float *d_vel, const float *d_dobs, float *d_data, float *d_image,
+                     void *d_ws, size_t ws_bytes, size_t budget_bytes, int32_t zchunk,
+                     rtm_stream stream);
 
 /* Size of the static device scratch of rtm_forward_noalloc: 24 MiB. */
 #define RTM_NOALLOC_SCRATCH_BYTES (24u << 20)

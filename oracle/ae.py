@@ -286,12 +286,20 @@ def unflatten(vec) -> Dict[str, np.ndarray]:
     return out
 
 
-def adam_step(params, grads, state, t: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
-    """One Adam update (Kingma and Ba, 2015) at step t >= 1, in place."""
+def adam_step(params, grads, state, t: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+              clip=None):
+    """One Adam update (Kingma and Ba, 2015) at step t >= 1, in place. With
+    ``clip`` the gradients are first scaled so that their joint L2 norm over
+    all parameters is at most ``clip``."""
+    scale = 1.0
+    if clip:
+        norm = math.sqrt(sum(float(np.sum(np.asarray(g, np.float64) ** 2)) for g in grads.values()))
+        if norm > clip:
+            scale = clip / norm
     for k in params:
         m = state.setdefault("m_" + k, np.zeros_like(params[k]))
         v = state.setdefault("v_" + k, np.zeros_like(params[k]))
-        g = grads[k]
+        g = grads[k] * scale
         m[...] = beta1 * m + (1 - beta1) * g
         v[...] = beta2 * v + (1 - beta2) * g * g
         mh = m / (1 - beta1 ** t)

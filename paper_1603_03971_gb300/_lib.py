@@ -84,6 +84,8 @@ SIGNATURES = {
     "rtm_backward_image_learned": (ctypes.c_int, [_P, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _vp]),
     "rtm_shot_learned": (ctypes.c_int, [_P, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _vp]),
     "rtm_snapshot": (ctypes.c_int, [_P, _vp, _sz, _i32, _vp, _vp]),
+    "rtm_batch_workspace_size": (_sz, [_P, _i32, _vp, _sz]),
+    "rtm_batch": (ctypes.c_int, [_P, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _sz, _i32, _vp]),
     "rtm_ae_param_count": (_sz, []),
     "rtm_ae_workspace_size": (_sz, [_i32, _i32, _i32]),
     "rtm_ae_encode": (ctypes.c_int, [_vp, _vp, _i64, _i64, _i32, _i32, _i32, _vp, _vp, _vp, _sz,

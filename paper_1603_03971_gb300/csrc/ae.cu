@@ -94,6 +94,18 @@ struct OpGemm {
             tc::st_vec8(sB, n, j * 8, v);
         }
     }
+    __device__ static void load_async(const Args& a, int m0, int ch, uint8_t* sA, uint8_t* sB,
+                                      int tid) {
+        const int r = m0 + tid;
+        const bf16* src = r < a.M ? a.A + (size_t)r * a.K + ch * 32 : a.A;
+#pragma unroll
+        for (int j = 0; j < 4; j++) tc::cp_async16(sA, tid, j * 8, src + j * 8, r < a.M);
+        if (tid < N * 4) {
+            const int n = tid >> 2, j = tid & 3;
+            uint4 v = *reinterpret_cast<const uint4*>(a.B + (size_t)n * a.K + ch * 32 + j * 8);
+            tc::st_vec8(sB, n, j * 8, v);
+        }
+    }
     __device__ static void epilogue(const Args& a, int m0, int row, const float* acc) {
         const int r = m0 + row;
         if (r >= a.M) return;
@@ -180,6 +192,9 @@ struct OpE2 {  // h1 -> latent
         }
 #pragma unroll
         for (int j = 0; j < 4; j++) tc::st_vec8(sA, tid, 8 * j, r[j]);
+        load_b(a, tap, sB, tid);
+    }
+    __device__ static void load_b(const Args& a, int tap, uint8_t* sB, int tid) {
         if (tid < 64) {
             const int o = tid >> 2, j = tid & 3;
             float w[8];
@@ -187,6 +202,26 @@ struct OpE2 {  // h1 -> latent
             for (int e = 0; e < 8; e++) w[e] = a.P[kOW2 + o * 864 + tap * 32 + 8 * j + e];
             tc::st_vec8(sB, o, 8 * j, tc::pack8(w));
         }
+    }
+    __device__ static void load_async(const Args& a, int m0, int tap, uint8_t* sA, uint8_t* sB,
+                                      int tid) {
+        const long long v = m0 + tid;
+        const long long total = (long long)a.l.nx * a.l.ny * a.l.nz;
+        const int kz = tap / 9, ky = (tap / 3) % 3, kx = tap % 3;
+        const bf16* src = a.h1;
+        bool ok = false;
+        if (v < total) {
+            int x, y, z;
+            decode3(v, a.l.nx, a.l.ny, x, y, z);
+            const int sx = 2 * x + kx - 1, sy = 2 * y + ky - 1, sz = 2 * z + kz - 1;
+            if (sx >= 0 && sx < a.h.nx && sy >= 0 && sy < a.h.ny && sz >= 0 && sz < a.h.nz) {
+                ok = true;
+                src = a.h1 + (((long long)sz * a.h.ny + sy) * a.h.nx + sx) * 32;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) tc::cp_async16(sA, tid, 8 * j, src + 8 * j, ok);
+        load_b(a, tap, sB, tid);
     }
     __device__ static void epilogue(const Args& a, int m0, int row, const float* acc) {
         const long long v = m0 + row;
@@ -231,6 +266,33 @@ struct OpD1 {  // latent -> g1, one output parity class per blockIdx.y
             tc::st_vec8(sA, tid, 16 * h, r0);
             tc::st_vec8(sA, tid, 16 * h + 8, r1);
         }
+        load_b(a, ch, sB, tid);
+    }
+    __device__ static void load_async(const Args& a, int m0, int ch, uint8_t* sA, uint8_t* sB,
+                                      int tid) {
+        const int q = blockIdx.y, qz = q >> 2, qy = (q >> 1) & 1, qx = q & 1;
+        const long long v = m0 + tid;
+        const long long total = (long long)a.l.nx * a.l.ny * a.l.nz;
+        int x = 0, y = 0, z = 0;
+        if (v < total) decode3(v, a.l.nx, a.l.ny, x, y, z);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int tau = 2 * ch + h;
+            int tz, kz, ty, ky, tx, kx;
+            convt_tap(qz, tau >> 2, tz, kz);
+            convt_tap(qy, (tau >> 1) & 1, ty, ky);
+            convt_tap(qx, tau & 1, tx, kx);
+            const int sx = x + tx, sy = y + ty, sz = z + tz;
+            const bool ok = v < total && sx >= 0 && sx < a.l.nx && sy >= 0 && sy < a.l.ny &&
+                            sz >= 0 && sz < a.l.nz;
+            const bf16* src = ok ? a.lat + (((long long)sz * a.l.ny + sy) * a.l.nx + sx) * 16 : a.lat;
+            tc::cp_async16(sA, tid, 16 * h, src, ok);
+            tc::cp_async16(sA, tid, 16 * h + 8, src + 8, ok);
+        }
+        load_b(a, ch, sB, tid);
+    }
+    __device__ static void load_b(const Args& a, int ch, uint8_t* sB, int tid) {
+        const int q = blockIdx.y, qz = q >> 2, qy = (q >> 1) & 1, qx = q & 1;
         {
             const int o = tid >> 2, j = tid & 3, h = j >> 1, i0 = (j & 1) * 8;
             const int tau = 2 * ch + h;
@@ -256,6 +318,49 @@ struct OpD1 {  // latent -> g1, one output parity class per blockIdx.y
 #pragma unroll
         for (int c = 0; c < 32; c++) f[c] = leaky(acc[c] + a.P[kOB3 + c]);
         store_bf16_row(a.g1 + o * 32, f, 32);
+    }
+};
+
+// D1 with D2 fused into its epilogue (inference): each accumulator row is a
+// g1 voxel (32 channels, rounded to bfloat16 as in the unfused pair), D2 maps
+// it to its 2 x 2 x 2 output block, so g1 never goes to memory
+struct OpD12 {
+    using Args = D12Args;
+    static constexpr int N = 32;
+    __device__ static void tile(const Args& a, int& m0, int& c0, int& c1) {
+        OpD1::tile(a.d1, m0, c0, c1);
+    }
+    __device__ static void load(const Args& a, int m0, int ch, uint8_t* sA, uint8_t* sB, int tid) {
+        OpD1::load(a.d1, m0, ch, sA, sB, tid);
+    }
+    __device__ static void load_async(const Args& a, int m0, int ch, uint8_t* sA, uint8_t* sB,
+                                      int tid) {
+        OpD1::load_async(a.d1, m0, ch, sA, sB, tid);
+    }
+    __device__ static void epilogue(const Args& a, int m0, int row, const float* acc) {
+        const D1Args& d = a.d1;
+        const long long v = m0 + row;
+        if (v >= (long long)d.l.nx * d.l.ny * d.l.nz) return;
+        const int q = blockIdx.y, qz = q >> 2, qy = (q >> 1) & 1, qx = q & 1;
+        int x, y, z;
+        decode3(v, d.l.nx, d.l.ny, x, y, z);
+        const int gx = 2 * x + qx, gy = 2 * y + qy, gz = 2 * z + qz;  // g1 voxel
+        float g[32];
+#pragma unroll
+        for (int c = 0; c < 32; c++)
+            g[c] = __bfloat162float(__float2bfloat16_rn(leaky(acc[c] + d.P[kOB3 + c])));
+        const float sc = a.sigma ? *a.sigma : 1.0f;
+        const float b = d.P[kOB4];
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            float yv = 0.f;
+#pragma unroll
+            for (int c = 0; c < 32; c++)
+                yv = fmaf(__bfloat162float(__float2bfloat16_rn(d.P[kOW4 + e * 32 + c])), g[c], yv);
+            const int ez = e >> 2, ey = (e >> 1) & 1, ex = e & 1;
+            a.out.p[(long long)(2 * gz + ez) * a.out.sz + (long long)(2 * gy + ey) * a.out.sy +
+                    2 * gx + ex] = sc * (yv + b);
+        }
     }
 };
 
@@ -380,6 +485,9 @@ struct OpD1d {  // ga3 -> glat: dlat[j] = sum_k W3[.,k,.]^T ga3[2j + k - 1]
         }
 #pragma unroll
         for (int j = 0; j < 4; j++) tc::st_vec8(sA, tid, 8 * j, r[j]);
+        load_b(a, ktap, sB, tid);
+    }
+    __device__ static void load_b(const Args& a, int ktap, uint8_t* sB, int tid) {
         if (tid < 64) {
             const int i = tid >> 2, j = tid & 3;
             float w[8];
@@ -387,6 +495,26 @@ struct OpD1d {  // ga3 -> glat: dlat[j] = sum_k W3[.,k,.]^T ga3[2j + k - 1]
             for (int e = 0; e < 8; e++) w[e] = a.P[kOW3 + (8 * j + e) * 1024 + ktap * 16 + i];
             tc::st_vec8(sB, i, 8 * j, tc::pack8(w));
         }
+    }
+    __device__ static void load_async(const Args& a, int m0, int ktap, uint8_t* sA, uint8_t* sB,
+                                      int tid) {
+        const long long v = m0 + tid;
+        const long long total = (long long)a.l.nx * a.l.ny * a.l.nz;
+        const int kz = ktap >> 4, ky = (ktap >> 2) & 3, kx = ktap & 3;
+        const bf16* src = a.ga3;
+        bool ok = false;
+        if (v < total) {
+            int x, y, z;
+            decode3(v, a.l.nx, a.l.ny, x, y, z);
+            const int ox = 2 * x + kx - 1, oy = 2 * y + ky - 1, oz = 2 * z + kz - 1;
+            if (ox >= 0 && ox < a.h.nx && oy >= 0 && oy < a.h.ny && oz >= 0 && oz < a.h.nz) {
+                ok = true;
+                src = a.ga3 + (((long long)oz * a.h.ny + oy) * a.h.nx + ox) * 32;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) tc::cp_async16(sA, tid, 8 * j, src + 8 * j, ok);
+        load_b(a, ktap, sB, tid);
     }
     __device__ static void epilogue(const Args& a, int m0, int row, const float* acc) {
         const long long v = m0 + row;
@@ -678,12 +806,23 @@ __global__ void k_small_grads(Vol in, const float* inv_sigma, const bf16* __rest
     }
 }
 
+__global__ void k_sumsq_vec(const float* __restrict__ g, int n, double* out) {
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        s += (double)g[i] * g[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+// Adam with the gradient scaled to a global L2 norm of at most clip
 __global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
                        const float* __restrict__ g, int n, float lr, float b1, float b2, float eps,
-                       float c1, float c2) {
+                       float c1, float c2, const double* gnorm2, float clip) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float gi = g[i];
+    const double nrm = sqrt(*gnorm2);
+    const float scale = (clip > 0.f && nrm > clip) ? (float)(clip / nrm) : 1.0f;
+    const float gi = g[i] * scale;
     const float mi = b1 * m[i] + (1.f - b1) * gi;
     const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
     m[i] = mi;
@@ -700,6 +839,12 @@ cudaError_t run(const typename Op::Args& a, dim3 grid, int* status, cudaStream_t
     return cudaGetLastError();
 }
 
+template <class Op>
+cudaError_t run_async(const typename Op::Args& a, dim3 grid, int* status, cudaStream_t s) {
+    tc::k_tc_gemm_async<Op><<<grid, 128, 0, s>>>(a, status);
+    return cudaGetLastError();
+}
+
 inline unsigned tiles(long long rows) { return (unsigned)((rows + 127) / 128); }
 
 }  // namespace ae
@@ -707,8 +852,8 @@ inline unsigned tiles(long long rows) { return (unsigned)((rows + 127) / 128); }
 using namespace ae;
 
 cudaError_t ae_gemm_test(const GemmArgs& a, int N, int* status, cudaStream_t s) {
-    if (N == 16) return run<OpGemm<16>>(a, dim3(tiles(a.M)), status, s);
-    if (N == 32) return run<OpGemm<32>>(a, dim3(tiles(a.M)), status, s);
+    if (N == 16) return run_async<OpGemm<16>>(a, dim3(tiles(a.M)), status, s);
+    if (N == 32) return run_async<OpGemm<32>>(a, dim3(tiles(a.M)), status, s);
     return cudaErrorInvalidValue;
 }
 
@@ -732,7 +877,7 @@ cudaError_t ae_encode(const float* P, const Vol& in, bf16* h1, bf16* lat, AeScal
     e = run<OpE1>(a1, dim3(tiles((long long)h.nx * h.ny * h.nz)), status, s);
     if (e != cudaSuccess) return e;
     E2Args a2{h1, h, P, lat, l};
-    e = run<OpE2>(a2, dim3(tiles((long long)l.nx * l.ny * l.nz)), status, s);
+    e = run_async<OpE2>(a2, dim3(tiles((long long)l.nx * l.ny * l.nz)), status, s);
     if (e != cudaSuccess) return e;
     if (sigma_out) e = cudaMemcpyAsync(sigma_out, &sc->sigma, sizeof(float),
                                        cudaMemcpyDeviceToDevice, s);
@@ -742,11 +887,16 @@ cudaError_t ae_encode(const float* P, const Vol& in, bf16* h1, bf16* lat, AeScal
 cudaError_t ae_decode(const float* P, const bf16* lat, const float* sigma, const Vol& out, bf16* g1,
                       int* status, cudaStream_t s) {
     const Dims3 h{out.nx / 2, out.ny / 2, out.nz / 2}, l{out.nx / 4, out.ny / 4, out.nz / 4};
-    D1Args a1{lat, l, P, g1, h};
-    cudaError_t e = run<OpD1>(a1, dim3(tiles((long long)l.nx * l.ny * l.nz), 8), status, s);
-    if (e != cudaSuccess) return e;
-    D2Args a2{g1, h, P, sigma, out};
-    return run<OpD2>(a2, dim3(tiles((long long)h.nx * h.ny * h.nz)), status, s);
+    if (g1) {  // two passes through g1 (training keeps g1 for the backward pass)
+        D1Args a1{lat, l, P, g1, h};
+        cudaError_t e =
+            run_async<OpD1>(a1, dim3(tiles((long long)l.nx * l.ny * l.nz), 8), status, s);
+        if (e != cudaSuccess) return e;
+        D2Args a2{g1, h, P, sigma, out};
+        return run<OpD2>(a2, dim3(tiles((long long)h.nx * h.ny * h.nz)), status, s);
+    }
+    D12Args a{D1Args{lat, l, P, nullptr, h}, sigma, out};
+    return run_async<OpD12>(a, dim3(tiles((long long)l.nx * l.ny * l.nz), 8), status, s);
 }
 
 // loss and gradient of one sample, accumulated into grad (scale = 1 / batch)
@@ -772,7 +922,7 @@ cudaError_t ae_sample_grad(const float* P, const Vol& in, float scale, const AeT
     if ((e = run<OpD1w>(w3, dim3(8, (nch_l + cpc_l - 1) / cpc_l), status, s)) != cudaSuccess)
         return e;
     D1dArgs d1{b.ga3, h, l, P, b.glat};
-    if ((e = run<OpD1d>(d1, dim3(tiles(nl)), status, s)) != cudaSuccess) return e;
+    if ((e = run_async<OpD1d>(d1, dim3(tiles(nl)), status, s)) != cudaSuccess) return e;
     E2wArgs w2{b.h1, h, b.glat, l, grad, cpc_l};
     if ((e = run<OpE2w>(w2, dim3(7, (nch_l + cpc_l - 1) / cpc_l), status, s)) != cudaSuccess)
         return e;
@@ -786,11 +936,15 @@ cudaError_t ae_sample_grad(const float* P, const Vol& in, float scale, const AeT
     return cudaGetLastError();
 }
 
-cudaError_t ae_adam(float* P, float* m, float* v, const float* g, int step, float lr,
-                    cudaStream_t s) {
+cudaError_t ae_adam(float* P, float* m, float* v, const float* g, int step, float lr, float clip,
+                    double* scratch, cudaStream_t s) {
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
-    k_adam<<<(kNParams + 255) / 256, 256, 0, s>>>(P, m, v, g, kNParams, lr, b1, b2, eps, c1, c2);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    k_sumsq_vec<<<64, 256, 0, s>>>(g, kNParams, scratch);
+    k_adam<<<(kNParams + 255) / 256, 256, 0, s>>>(P, m, v, g, kNParams, lr, b1, b2, eps, c1, c2,
+                                                  scratch, clip);
     return cudaGetLastError();
 }
 

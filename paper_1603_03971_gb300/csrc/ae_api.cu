@@ -15,6 +15,7 @@ using namespace rtm::ae;
 namespace {
 
 constexpr size_t kAl = 256;
+constexpr float kGradClip = 1.0f;  // global gradient-norm bound of each Adam step
 size_t upa(size_t v) { return (v + kAl - 1) / kAl * kAl; }
 
 struct AeLayout {
@@ -96,6 +97,7 @@ rtm_status rtm_ae_encode(const float* d_params, const float* d_snap, int64_t sy,
         return (rtm_status)set_error(RTM_ERR_INVALID, "snapshot strides overlap rows or planes");
     char* w = reinterpret_cast<char*>(d_ws);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaGetLastError();
     const Vol in{const_cast<float*>(d_snap), sy, sz, nx, ny, nz};
     CUA(cudaMemsetAsync(w, 0, sizeof(int), s));
     CUA(ae_encode(d_params, in, reinterpret_cast<bf16*>(w + L.h1), reinterpret_cast<bf16*>(d_latent),
@@ -117,10 +119,11 @@ rtm_status rtm_ae_decode(const float* d_params, const uint16_t* d_latent, const 
         return (rtm_status)set_error(RTM_ERR_INVALID, "output strides overlap rows or planes");
     char* w = reinterpret_cast<char*>(d_ws);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaGetLastError();
     const Vol out{d_out, sy, sz, nx, ny, nz};
     CUA(cudaMemsetAsync(w, 0, sizeof(int), s));
-    CUA(ae_decode(d_params, reinterpret_cast<const bf16*>(d_latent), d_scale, out,
-                  reinterpret_cast<bf16*>(w + L.g1), reinterpret_cast<int*>(w + L.status), s));
+    CUA(ae_decode(d_params, reinterpret_cast<const bf16*>(d_latent), d_scale, out, nullptr,
+                  reinterpret_cast<int*>(w + L.status), s));
     return RTM_OK;
 }
 
@@ -138,6 +141,7 @@ rtm_status rtm_ae_train_step(float* d_params, float* d_adam_m, float* d_adam_v, 
         return (rtm_status)set_error(RTM_ERR_INVALID, "Adam needs moment buffers and step >= 1");
     char* w = reinterpret_cast<char*>(d_ws);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaGetLastError();
     float* grad = reinterpret_cast<float*>(w + L.grad);
     AeTrainBufs b{reinterpret_cast<bf16*>(w + L.h1),  reinterpret_cast<bf16*>(w + L.lat),
                   reinterpret_cast<bf16*>(w + L.g1),  reinterpret_cast<bf16*>(w + L.gy),
@@ -156,7 +160,9 @@ rtm_status rtm_ae_train_step(float* d_params, float* d_adam_m, float* d_adam_v, 
     }
     if (d_grad)
         CUA(cudaMemcpyAsync(d_grad, grad, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, s));
-    if (lr > 0.f) CUA(ae_adam(d_params, d_adam_m, d_adam_v, grad, step, lr, s));
+    if (lr > 0.f)
+        CUA(ae_adam(d_params, d_adam_m, d_adam_v, grad, step, lr, kGradClip,
+                    reinterpret_cast<double*>(w + L.scalars + 128), s));
     return RTM_OK;
 }
 

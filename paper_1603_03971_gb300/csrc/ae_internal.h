@@ -37,6 +37,7 @@ struct E1Args { Vol in; const float* inv_sigma; const float* P; bf16* h1; Dims3 
 struct E2Args { const bf16* h1; Dims3 h; const float* P; bf16* lat; Dims3 l; };
 struct D1Args { const bf16* lat; Dims3 l; const float* P; bf16* g1; Dims3 h; };
 struct D2Args { const bf16* g1; Dims3 h; const float* P; const float* sigma; Vol out; };
+struct D12Args { D1Args d1; const float* sigma; Vol out; };
 struct D2dArgs { const bf16* gy; Dims3 h; const bf16* g1; const float* P; bf16* ga3; };
 struct D1dArgs { const bf16* ga3; Dims3 h; Dims3 l; const float* P; bf16* glat; };
 struct E2dArgs { const bf16* glat; Dims3 l; const bf16* h1; Dims3 h; const float* P; bf16* ga1; };
@@ -63,13 +64,16 @@ cudaError_t ae_rms(const ae::Vol& in, ae::AeScalars* sc, cudaStream_t s);
 // snapshot -> latent (h1 is scratch); the snapshot's rms goes to sigma_out if given
 cudaError_t ae_encode(const float* P, const ae::Vol& in, ae::bf16* h1, ae::bf16* lat,
                       ae::AeScalars* sc, float* sigma_out, int* status, cudaStream_t s);
-// latent -> snapshot scaled by *sigma (1 if NULL); g1 is scratch
+// latent -> snapshot scaled by *sigma (1 if NULL); with g1 NULL the two
+// decoder layers run fused (inference), otherwise g1 keeps the D1 output
 cudaError_t ae_decode(const float* P, const ae::bf16* lat, const float* sigma, const ae::Vol& out,
                       ae::bf16* g1, int* status, cudaStream_t s);
 cudaError_t ae_sample_grad(const float* P, const ae::Vol& in, float scale,
                            const ae::AeTrainBufs& b, ae::AeScalars* sc, double* loss, float* grad,
                            int* status, cudaStream_t s);
-cudaError_t ae_adam(float* P, float* m, float* v, const float* g, int step, float lr,
-                    cudaStream_t s);
+// Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with the gradient
+// scaled down to a global L2 norm of clip when it is larger (clip <= 0: off)
+cudaError_t ae_adam(float* P, float* m, float* v, const float* g, int step, float lr, float clip,
+                    double* scratch, cudaStream_t s);
 
 }  // namespace rtm

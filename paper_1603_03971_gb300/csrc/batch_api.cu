@@ -1,0 +1,332 @@
+// C ABI of the batched multi-shot RTM: wave planning under a memory budget,
+// per-shot buffers, the common phase schedule, and one CUDA graph per call
+// holding every wave's model preparation, persistent launch and image stack.
+
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/rtm.h"
+#include "batch_internal.h"
+
+using namespace rtm;
+
+namespace {
+
+constexpr size_t kAlB = 256;
+constexpr int kMaxShotsTotal = 1024;
+size_t upb(size_t v) { return (v + kAlB - 1) / kAlB * kAlB; }
+
+#define CUB(call)                                                                       \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return (rtm_status)set_error(RTM_ERR_CUDA, "%s failed: %s", #call,          \
+                                         cudaGetErrorString(e_));                       \
+    } while (0)
+
+struct Plan {
+    std::vector<BatchShot> shots;     // pointers filled per wave
+    std::vector<size_t> bytes;        // per-shot buffer bytes
+    std::vector<size_t> data_off;     // offset (floats) of each shot's data
+    std::vector<std::pair<int, int>> waves;  // [first, last) shots
+    std::vector<BatchPhase> phases;
+    size_t pool = 0;                  // largest wave
+    size_t off_ctrl, off_phases, off_desc, off_wav, off_pool, total;
+};
+
+void weights_b(int r, double* a) {
+    double fr = 1.0;
+    for (int i = 2; i <= r; i++) fr *= i;
+    double sum = 0.0;
+    for (int k = 1; k <= r; k++) {
+        double f1 = 1.0, f2 = 1.0;
+        for (int i = 2; i <= r - k; i++) f1 *= i;
+        for (int i = 2; i <= r + k; i++) f2 *= i;
+        a[k] = 2.0 * ((k % 2 == 1) ? 1.0 : -1.0) * fr * fr / ((double)k * k * f1 * f2);
+        sum += a[k];
+    }
+    a[0] = -2.0 * sum;
+}
+
+rtm_status check_batch(const rtm_params* p, int nshots, const rtm_aperture* sh) {
+    rtm_params q = *p;
+    q.storage = RTM_STORE_CKPT;
+    q.src_x = q.src_y = q.src_z = 0;
+    q.want_grad = 0;
+    q.nb = 0;  // the full model itself is not padded
+    q.nx += (4 - q.nx % 4) % 4;  // only the apertures' rows must be 16-byte aligned
+    rtm_status st = rtm_validate(&q);
+    if (st != RTM_OK) return st;
+    if (p->storage != RTM_STORE_CKPT || p->ckpt_every < 1)
+        return (rtm_status)set_error(RTM_ERR_INVALID, "the batch checkpoints: storage must be "
+                                                      "RTM_STORE_CKPT with ckpt_every >= 1");
+    if (nshots < 1 || nshots > kMaxShotsTotal || !sh)
+        return (rtm_status)set_error(RTM_ERR_INVALID, "nshots %d out of [1, %d]", nshots,
+                                     kMaxShotsTotal);
+    for (int s = 0; s < nshots; s++) {
+        const rtm_aperture& a = sh[s];
+        if (a.nx < 1 || a.ny < 1 || a.nz < 1 || a.ox < 0 || a.oy < 0 || a.oz < 0 ||
+            a.ox + a.nx > p->nx || a.oy + a.ny > p->ny || a.oz + a.nz > p->nz)
+            return (rtm_status)set_error(RTM_ERR_INVALID, "aperture %d outside the model", s);
+        if ((a.nx + 2 * p->nb) % 4)
+            return (rtm_status)set_error(RTM_ERR_INVALID,
+                                         "aperture %d: nx + 2 nb must be a multiple of 4", s);
+        if (a.src_x < 0 || a.src_x >= a.nx || a.src_y < 0 || a.src_y >= a.ny || a.src_z < 0 ||
+            a.src_z >= a.nz || a.rec_z < 0 || a.rec_z >= a.nz)
+            return (rtm_status)set_error(RTM_ERR_INVALID, "aperture %d: source or receiver "
+                                                          "plane outside the aperture", s);
+    }
+    return RTM_OK;
+}
+
+Plan make_plan(const rtm_params* p, int nshots, const rtm_aperture* sh, size_t budget,
+               int zchunk) {
+    Plan P;
+    const int R = p->radius, k = p->ckpt_every, nt = p->nt;
+    const int nseg = (nt + k - 1) / k;
+    size_t doff = 0;
+    for (int s = 0; s < nshots; s++) {
+        BatchShot b;
+        memset(&b, 0, sizeof b);
+        b.nb = p->nb;
+        b.nx = sh[s].nx;
+        b.ny = sh[s].ny;
+        b.nz = sh[s].nz;
+        b.NX = b.nx + 2 * p->nb;
+        b.NY = b.ny + 2 * p->nb;
+        b.NZ = b.nz + 2 * p->nb;
+        b.tiles_x = (b.NX + 63) / 64;
+        b.tiles_y = (b.NY + 15) / 16;
+        b.tiles_z = (b.NZ + zchunk - 1) / zchunk;
+        b.ntiles = b.tiles_x * b.tiles_y * b.tiles_z;
+        b.src_x = sh[s].src_x + p->nb;
+        b.src_y = sh[s].src_y + p->nb;
+        b.src_z = sh[s].src_z + p->nb;
+        b.rec_z = sh[s].rec_z + p->nb;
+        const size_t N = (size_t)b.NX * b.NY * b.NZ;
+        const size_t slab = (size_t)b.nz * b.ny * b.NX;
+        size_t bytes = upb(4 * N);                                       // c
+        bytes += upb(4 * (size_t)b.NX) + upb(4 * (size_t)b.NY) + upb(4 * (size_t)b.NZ);
+        bytes += 4 * upb(4 * N);                                         // fields
+        bytes += upb(4 * N * 2 * (size_t)(nseg > 1 ? nseg - 1 : 0));     // checkpoints
+        bytes += upb(4 * slab * (size_t)k);                              // snapshots
+        bytes += upb(4 * slab);                                          // image slab
+        P.shots.push_back(b);
+        P.bytes.push_back(bytes);
+        P.data_off.push_back(doff);
+        doff += (size_t)nt * b.nx * b.ny;
+        (void)R;
+    }
+    // waves: consecutive shots while the budget holds (a shot over budget alone)
+    int first = 0;
+    size_t acc = 0;
+    for (int s = 0; s < nshots; s++) {
+        const bool full = (s - first) >= kMaxBatchShots;
+        if (s > first && (full || (budget && acc + P.bytes[s] > budget))) {
+            P.waves.push_back({first, s});
+            P.pool = std::max(P.pool, acc);
+            first = s;
+            acc = 0;
+        }
+        acc += P.bytes[s];
+    }
+    P.waves.push_back({first, nshots});
+    P.pool = std::max(P.pool, acc);
+    // phase schedule
+    for (int n = 0; n < nt; n++) P.phases.push_back({PH_FWD, n, 0, 0});
+    for (int j = nseg - 1; j >= 0; j--) {
+        const int n0 = j * k, n1 = std::min(nt, n0 + k);
+        for (int n = n0; n < n1; n++) P.phases.push_back({PH_REC, n, j, n - n0});
+        for (int m = n1; m > n0; m--) P.phases.push_back({PH_BWD, m, j, m - 1 - n0});
+    }
+    size_t off = kAlB;  // status block
+    P.off_ctrl = off;
+    off += upb(sizeof(BatchCtrl));
+    P.off_phases = off;
+    off += upb(sizeof(BatchPhase) * P.phases.size());
+    P.off_desc = off;
+    off += upb(sizeof(BatchShot) * (size_t)nshots);
+    P.off_wav = off;
+    off += upb(sizeof(float) * (size_t)nt);
+    P.off_pool = off;
+    off += P.pool;
+    P.total = off;
+    return P;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t rtm_batch_workspace_size(const rtm_params* p, int32_t nshots, const rtm_aperture* h_shots,
+                                size_t budget_bytes) {
+    if (!p || check_batch(p, nshots, h_shots) != RTM_OK) return 0;
+    return make_plan(p, nshots, h_shots, budget_bytes, auto_zchunk(p->radius, 64, 16, 1 << 20))
+        .total;
+}
+
+rtm_status rtm_batch(const rtm_params* p, int32_t nshots, const rtm_aperture* h_shots,
+                     const float* d_vel, const float* d_dobs, float* d_data, float* d_image,
+                     void* d_ws, size_t ws_bytes, size_t budget_bytes, int32_t zchunk,
+                     rtm_stream stream) {
+    if (!p) return (rtm_status)set_error(RTM_ERR_INVALID, "params is NULL");
+    rtm_status st = check_batch(p, nshots, h_shots);
+    if (st != RTM_OK) return st;
+    if (!d_vel || !d_dobs || !d_image)
+        return (rtm_status)set_error(RTM_ERR_INVALID, "batch arrays are NULL");
+    const int zc_default = auto_zchunk(p->radius, 64, 16, 1 << 20);
+    if (zchunk < 0) return (rtm_status)set_error(RTM_ERR_INVALID, "zchunk < 0");
+    const int zc = zchunk > 0 ? zchunk : zc_default;
+    Plan P = make_plan(p, nshots, h_shots, budget_bytes, zc_default);
+    if (zc != zc_default) {
+        // the workspace was sized with the default slab height; only the
+        // tile counts change with zchunk
+        for (auto& b : P.shots) {
+            b.tiles_z = (b.NZ + zc - 1) / zc;
+            b.ntiles = b.tiles_x * b.tiles_y * b.tiles_z;
+        }
+    }
+    if (!d_ws || ((uintptr_t)d_ws % kAlB))
+        return (rtm_status)set_error(RTM_ERR_WORKSPACE, "workspace NULL or not 256-byte aligned");
+    if (ws_bytes < P.total)
+        return (rtm_status)set_error(RTM_ERR_WORKSPACE, "batch workspace %zu bytes, %zu needed",
+                                     ws_bytes, P.total);
+    for (auto& w : P.waves)
+        if (w.second - w.first > kMaxBatchShots)
+            return (rtm_status)set_error(RTM_ERR_INVALID, "wave too large");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char* ws = reinterpret_cast<char*>(d_ws);
+    cudaGetLastError();  // a stale error of earlier work must not be taken for ours
+    int dev = 0, nsm = 0;
+    CUB(cudaGetDevice(&dev));
+    CUB(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int bps = batch_blocks_per_sm(p->radius);
+    if (bps < 1) return (rtm_status)set_error(RTM_ERR_CUDA, "batch kernel does not fit on an SM");
+    int clock_khz = 0;
+    CUB(cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev));
+
+    // per-wave buffer pointers and descriptors (all waves share the pool)
+    for (auto& w : P.waves) {
+        char* q = ws + P.off_pool;
+        long long base = 0;
+        for (int i = w.first; i < w.second; i++) {
+            BatchShot& b = P.shots[i];
+            const size_t N = (size_t)b.NX * b.NY * b.NZ;
+            const size_t slab = (size_t)b.nz * b.ny * b.NX;
+            const int nseg = (p->nt + p->ckpt_every - 1) / p->ckpt_every;
+            auto take = [&](size_t bytes) {
+                char* r = q;
+                q += upb(bytes);
+                return reinterpret_cast<float*>(r);
+            };
+            b.c = take(4 * N);
+            b.gx = take(4 * (size_t)b.NX);
+            b.gy = take(4 * (size_t)b.NY);
+            b.gz = take(4 * (size_t)b.NZ);
+            b.f0 = take(4 * N);
+            b.f1 = take(4 * N);
+            b.m0 = take(4 * N);
+            b.m1 = take(4 * N);
+            b.ckpt = take(4 * N * 2 * (size_t)(nseg > 1 ? nseg - 1 : 0));
+            b.snap = take(4 * slab * (size_t)p->ckpt_every);
+            b.img = take(4 * slab);
+            b.dobs = d_dobs + P.data_off[i];
+            b.data = d_data ? d_data + P.data_off[i] : nullptr;
+            b.item_base = base;
+            base += b.ntiles;
+        }
+    }
+    // static tables (before capture: host sources stay valid until the sync)
+    CUB(cudaMemcpyAsync(ws + P.off_phases, P.phases.data(), sizeof(BatchPhase) * P.phases.size(),
+                        cudaMemcpyHostToDevice, s));
+    CUB(cudaMemcpyAsync(ws + P.off_desc, P.shots.data(), sizeof(BatchShot) * P.shots.size(),
+                        cudaMemcpyHostToDevice, s));
+    CUB(cudaMemsetAsync(ws, 0, sizeof(int), s));
+    CUB(launch_wavelet(p->nt, p->dt, p->f0, p->t0, reinterpret_cast<float*>(ws + P.off_wav), s));
+    CUB(cudaStreamSynchronize(s));
+
+    BatchArgs A;
+    memset(&A, 0, sizeof A);
+    double a[kMaxRadius + 1];
+    weights_b(p->radius, a);
+    const double inv_dx2 = 1.0 / (p->dx * p->dx);
+    A.a[0] = (float)(3.0 * a[0] * inv_dx2);
+    for (int k = 1; k <= p->radius; k++) A.a[k] = (float)(a[k] * inv_dx2);
+    A.inv_dx3 = (float)(1.0 / (p->dx * p->dx * p->dx));
+    A.phases = reinterpret_cast<const BatchPhase*>(ws + P.off_phases);
+    A.nphases = (int)P.phases.size();
+    A.ctrl = reinterpret_cast<BatchCtrl*>(ws + P.off_ctrl);
+    A.wavelet = reinterpret_cast<const float*>(ws + P.off_wav);
+    A.zchunk = zc;
+    A.ckpt_every = p->ckpt_every;
+    A.image_every = p->image_every;
+    A.nt = p->nt;
+    A.timeout_cycles = (long long)clock_khz * 1000LL * 20;  // about 20 s at the base clock
+    A.status = reinterpret_cast<int*>(ws);
+
+    // capture on a private stream (the caller's may be the legacy default
+    // stream, which cannot be captured); the graph runs on the caller's stream
+    cudaStream_t cs = nullptr;
+    CUB(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    {
+        cudaError_t eb = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (eb != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            return (rtm_status)set_error(RTM_ERR_CUDA, "batch capture: %s", cudaGetErrorString(eb));
+        }
+    }
+    const cudaStream_t s_caller = s;
+    s = cs;
+    cudaError_t err = cudaSuccess;
+    for (auto& w : P.waves) {
+        long long items = 0;
+        for (int i = w.first; i < w.second && err == cudaSuccess; i++) {
+            const BatchShot& b = P.shots[i];
+            items += b.ntiles;
+            err = launch_batch_prep(b, d_vel, p->nx, p->ny, h_shots[i].ox, h_shots[i].oy,
+                                    h_shots[i].oz, p->dt, const_cast<float*>(b.c),
+                                    const_cast<float*>(b.gx), const_cast<float*>(b.gy),
+                                    const_cast<float*>(b.gz), s);
+            if (err == cudaSuccess)
+                err = cudaMemsetAsync(b.img, 0, 4 * (size_t)b.nz * b.ny * b.NX, s);
+        }
+        if (err != cudaSuccess) break;
+        err = cudaMemsetAsync(A.ctrl, 0, sizeof(BatchCtrl), s);
+        if (err != cudaSuccess) break;
+        A.shots = reinterpret_cast<const BatchShot*>(ws + P.off_desc) + w.first;
+        A.nshots = w.second - w.first;
+        A.items_per_phase = items;
+        err = launch_batch(p->radius, A, nsm * bps, s);
+        for (int i = w.first; i < w.second && err == cudaSuccess; i++)
+            err = launch_batch_image_add(P.shots[i], p->nx, p->ny, h_shots[i].ox, h_shots[i].oy,
+                                         h_shots[i].oz, d_image, s);
+        if (err != cudaSuccess) break;
+    }
+    cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    s = s_caller;
+    if (err != cudaSuccess || ec != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return (rtm_status)set_error(RTM_ERR_CUDA, "batch graph capture failed: %s",
+                                     cudaGetErrorString(err != cudaSuccess ? err : ec));
+    }
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess)
+        return (rtm_status)set_error(RTM_ERR_CUDA, "batch graph instantiate failed: %s",
+                                     cudaGetErrorString(ei));
+    cudaError_t el = cudaGraphLaunch(exec, s);
+    cudaError_t es = el == cudaSuccess ? cudaStreamSynchronize(s) : el;
+    cudaGraphExecDestroy(exec);
+    if (es != cudaSuccess)
+        return (rtm_status)set_error(RTM_ERR_CUDA, "batch graph failed: %s", cudaGetErrorString(es));
+    return RTM_OK;
+}
+
+}  // extern "C"

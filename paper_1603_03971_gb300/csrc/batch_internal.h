@@ -1,0 +1,70 @@
+// Internal declarations of the batched multi-shot RTM kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rtm_internal.h"
+
+namespace rtm {
+
+constexpr int kMaxBatchShots = 64;
+
+// one shot of a wave: its padded aperture grid and its buffers
+struct BatchShot {
+    int NX, NY, NZ, nb, nx, ny, nz;
+    int tiles_x, tiles_y, tiles_z, ntiles;
+    int src_x, src_y, src_z;  // padded coordinates
+    int rec_z;                // padded z of the receiver plane (every model x, y)
+    long long item_base;      // first tile of this shot within one phase step
+    const float* c;
+    float *f0, *f1, *m0, *m1;  // forward and backward field pairs
+    float* ckpt;               // (nseg - 1) checkpoints of two fields
+    float* snap;               // ckpt_every snapshot slabs [nz][ny][NX]
+    float* img;                // image slab
+    const float *gx, *gy, *gz;
+    const float* dobs;         // [nt][ny][nx] data injected backward
+    float* data;               // [nt][ny][nx] modelled data, or NULL
+};
+
+// phase step of the common schedule: forward steps, then per checkpoint
+// segment (last first) its recompute steps and its backward steps
+enum BatchPhaseKind { PH_FWD = 0, PH_REC = 1, PH_BWD = 2 };
+struct BatchPhase {
+    int kind;
+    int step;   // n (forward, recompute) or m (backward)
+    int seg;    // checkpoint segment j (recompute, backward)
+    int local;  // n - n0 (recompute) or m - 1 - n0 (backward): the snapshot slot
+};
+
+struct BatchCtrl {
+    unsigned long long next;  // work-queue head
+    int abort;                // set when a bounded wait ran out
+    int status;               // RTM_ERR_TIMEOUT if so
+    unsigned int done[kMaxBatchShots];  // completed tiles per shot
+};
+
+struct BatchArgs {
+    const BatchShot* shots;
+    int nshots;
+    const BatchPhase* phases;
+    int nphases;
+    long long items_per_phase;
+    BatchCtrl* ctrl;
+    const float* wavelet;
+    float a[kMaxRadius + 1];
+    float inv_dx3;
+    int zchunk, ckpt_every, image_every, nt;
+    long long timeout_cycles;
+    int* status;  // workspace status word (RTM_ERR_TIMEOUT on a wait that ran out)
+};
+
+cudaError_t launch_batch(int radius, const BatchArgs& a, int grid, cudaStream_t s);
+int batch_blocks_per_sm(int radius);
+cudaError_t launch_batch_prep(const BatchShot& sh, const float* vel_full, int full_nx, int full_ny,
+                              int ox, int oy, int oz, double dt, float* c, float* gx, float* gy,
+                              float* gz, cudaStream_t s);
+cudaError_t launch_batch_image_add(const BatchShot& sh, int full_nx, int full_ny, int ox, int oy,
+                                   int oz, float* image_full, cudaStream_t s);
+
+}  // namespace rtm

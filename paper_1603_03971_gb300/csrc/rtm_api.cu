@@ -286,6 +286,7 @@ struct Ctx {
 };
 
 rtm_status make_ctx(Ctx& C, const rtm_params* p, const float* c, void* ws, rtm_stream s) {
+    cudaGetLastError();  // a stale error of earlier work must not be taken for ours
     C.p = p;
     C.d = dims_of(p);
     C.L = layout_of(p);
@@ -480,8 +481,8 @@ rtm_status run_backward(Ctx& C, const int32_t* rec, const float* rdata, float* s
             if (m % ie == 0) {
                 const size_t k = (size_t)(m / ie - 1);
                 CU(ae_decode(C.ae, C.latent_slot(k), C.at(C.L.scales) + k, C.model_view(slab),
-                             reinterpret_cast<ae::bf16*>(C.at(C.L.ae_h)), C.status(), C.s));
-                count_launch(2);
+                             nullptr, C.status(), C.s));
+                count_launch(1);
             }
             CHECK(back_step(m, slab));
         }
@@ -589,6 +590,7 @@ rtm_status rtm_model_prep(const rtm_params* p, const float* d_vel, int32_t vel_k
     if (!d_ws || ws_bytes < kStatusBytes) return fail(RTM_ERR_WORKSPACE, "workspace missing");
     if ((uintptr_t)d_ws % kAlign) return fail(RTM_ERR_WORKSPACE, "workspace not 256-byte aligned");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaGetLastError();
     const Dims d = dims_of(p);
     Geometry G{d.NX, d.NY, d.NZ, p->nb, p->nx, p->ny, p->nz};
     // reduction words in the status block of the workspace

@@ -158,6 +158,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* out) {
     for (int i = 0; i < 16; i++) out[i] = __uint_as_float(r[i]);
 }
 
+// 16-byte asynchronous global -> shared copy; zero-fills when !valid (the
+// source is not read then, but must still be a mapped address)
+__device__ __forceinline__ void cp_async16(uint8_t* slab, int r, int k, const void* src, bool valid) {
+    const uint32_t dst = smem_u32(slab + kmajor_off(r, k));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Op interface:
 //   using Args;                      kernel arguments
 //   static constexpr int N;          16 or 32 output columns
@@ -216,6 +232,105 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const __grid_constant__ typenam
     if (issued > 0) {
         const int last = issued - 1;
         const bool done = mbar_wait(&bars[last % kStages], (uint32_t)((last / kStages) & 1));
+        ok = ok && done;
+    }
+    ok = __syncthreads_and(ok);
+    tc_fence_after();
+
+    float acc[N];
+    if (ok && nch > 0) {
+        const uint32_t t = tmem + ((uint32_t)(warp * 32) << 16);
+        tmem_ld16(t, acc);
+        if constexpr (N == 32) tmem_ld16(t + 16, acc + 16);
+    } else {
+#pragma unroll
+        for (int n = 0; n < N; n++) acc[n] = 0.0f;
+    }
+    if (ok) Op::epilogue(args, m0, tid, acc);
+    else if (tid == 0 && status) atomicCAS(status, 0, kErrTimeout);
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+}  // namespace tc
+}  // namespace rtm
+
+namespace rtm {
+namespace tc {
+
+// The same engine with a deeper, asynchronous operand pipeline for ops whose
+// A slabs are plain 16-byte gathers: Op::load_async issues cp.async copies
+// for A (and stores B synchronously); kAsyncStages slabs are in flight while
+// the tensor core works on the oldest. The stage of slab j is refilled only
+// after the MMAs of slab j - kAsyncStages have completed (their commit
+// mbarrier); every wait is bounded as in k_tc_gemm.
+constexpr int kAsyncStages = 4;
+
+template <class Op>
+__global__ void __launch_bounds__(128) k_tc_gemm_async(const __grid_constant__ typename Op::Args args,
+                                                       int* status) {
+    constexpr int N = Op::N;
+    constexpr int S = kAsyncStages;
+    static_assert(N == 16 || N == 32, "N must be 16 or 32");
+    __shared__ __align__(1024) uint8_t smem[S][kStageBytes];
+    __shared__ __align__(8) uint64_t bars[S];
+    __shared__ uint32_t tmem_slot;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    int m0, c0, c1;
+    Op::tile(args, m0, c0, c1);
+    const int nch = c1 - c0;
+
+    if (tid == 0) {
+        for (int s = 0; s < S; s++) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(&tmem_slot, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    constexpr uint32_t idesc = idesc_bf16(kRows, N);
+
+    for (int c = 0; c < S - 1; c++) {
+        if (c < nch) Op::load_async(args, m0, c0 + c, smem[c], smem[c] + kABytes, tid);
+        cp_async_commit();
+    }
+    bool ok = true;
+    int issued = 0;
+    for (int i = 0; i < nch && ok; i++) {
+        const int j = i + S - 1;
+        if (j < nch) {
+            // slab j reuses the stage of slab i - 1
+            if (i >= 1) ok = mbar_wait(&bars[(i - 1) % S], (uint32_t)(((i - 1) / S) & 1));
+            ok = __syncthreads_and(ok);
+            if (!ok) break;
+            Op::load_async(args, m0, c0 + j, smem[j % S], smem[j % S] + kABytes, tid);
+        }
+        cp_async_commit();
+        cp_async_wait<S - 1>();
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const int st = i % S;
+            const uint32_t a0 = smem_u32(smem[st]);
+            const uint32_t b0 = a0 + kABytes;
+#pragma unroll
+            for (int s = 0; s < kBK / 16; s++) {
+                mma_bf16(tmem, sdesc(a0 + 256 * s, 128, 512), sdesc(b0 + 256 * s, 128, 512),
+                         idesc, (i > 0 || s > 0) ? 1u : 0u);
+            }
+            mma_commit(&bars[st]);
+        }
+        issued = i + 1;
+    }
+    cp_async_wait<0>();
+    if (issued > 0) {
+        const int last = issued - 1;
+        const bool done = mbar_wait(&bars[last % S], (uint32_t)((last / S) & 1));
         ok = ok && done;
     }
     ok = __syncthreads_and(ok);

@@ -28,7 +28,7 @@ def training_snapshots(n_models: int = 64, size: int = 192, nb: int = 32, nt: in
     """Snapshots [S][size][size][size] (float32, on the device) of forward
     modelling on ``n_models`` seeded smooth random models (sigma 8 cells,
     [vmin, vmax]); one surface source per model at a seeded position; the
-    snapshots at steps first, first + every, ..., nt."""
+    snapshots at the multiples of ``every`` from ``first`` to ``nt``."""
     dt = rtm_inputs.courant_dt(dx, vmax)
     rng = np.random.Generator(np.random.PCG64(seed0))
     out: List[torch.Tensor] = []
@@ -43,7 +43,7 @@ def training_snapshots(n_models: int = 64, size: int = 192, nb: int = 32, nt: in
         c = model_prep(p, v.contiguous(), ws)
         rec = torch.tensor([[size // 2, size // 2, 2]], dtype=torch.int32, device=device)
         forward(p, c, rec, ws)
-        for m in range(first, nt + 1, every):
+        for m in range(every * max(1, -(-first // every)), nt + 1, every):
             out.append(snapshot(p, ws, m).clone())
         del ws, c, v
     return torch.stack(out)

@@ -151,5 +151,5 @@ def test_adam_step_matches_oracle():
     torch.cuda.synchronize()
     g = grad.cpu().numpy().astype(np.float64)
     ref = {"w": P0.astype(np.float32).astype(np.float64)}
-    oae.adam_step(ref, {"w": g}, {}, 1, lr=1e-3)
+    oae.adam_step(ref, {"w": g}, {}, 1, lr=1e-3, clip=1.0)
     np.testing.assert_allclose(P.cpu().numpy(), ref["w"], rtol=1e-5, atol=1e-7)

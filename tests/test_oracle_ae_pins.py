@@ -165,3 +165,21 @@ def test_layers_on_non_cubic_volumes_match_torch():
     np.testing.assert_allclose(y, yt[0, 0].numpy(), rtol=1e-10, atol=1e-10)
     L, grads = ae.loss_and_grads(P, x, bf16=False)
     assert np.isfinite(L) and all(np.isfinite(v).all() for v in grads.values())
+
+
+def test_adam_with_gradient_clipping_matches_torch():
+    rng = np.random.default_rng(13)
+    p0 = {"a": rng.standard_normal(20), "b": rng.standard_normal(7)}
+    P = {k: torch.nn.Parameter(_t(v)) for k, v in p0.items()}
+    opt = torch.optim.Adam(list(P.values()), lr=0.01)
+    q = {k: v.copy() for k, v in p0.items()}
+    st = {}
+    for t in range(1, 6):
+        g = {k: rng.standard_normal(v.shape) * 3.0 for k, v in p0.items()}
+        for k in P:
+            P[k].grad = _t(g[k])
+        torch.nn.utils.clip_grad_norm_(list(P.values()), 1.0)
+        opt.step()
+        ae.adam_step(q, g, st, t, lr=0.01, clip=1.0)
+    for k in P:
+        np.testing.assert_allclose(q[k], P[k].detach().numpy(), rtol=1e-9, atol=1e-12)
