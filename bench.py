@@ -50,6 +50,15 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-steps", type=int, default=2,
                     help="oracle time steps per bench step of the reference arm")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-compression leg (384^3, 3000 steps)")
+    ap.add_argument("--learned-train-steps", type=int, default=2000)
+    ap.add_argument("--learned-models", type=int, default=24)
+    ap.add_argument("--batch", action="store_true",
+                    help="also run the batched-shots leg (32 apertures, radius 8)")
+    ap.add_argument("--batch-nt", type=int, default=1500)
+    ap.add_argument("--variant", type=int, default=0,
+                    help="stencil plane-load variant: 0 automatic, 1 vector loads, 2 TMA")
     return ap.parse_args()
 
 
@@ -242,6 +251,121 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------
+# learned snapshot compression vs checkpoint recompute (384^3, 3000 steps)
+# ----------------------------------------------------------------------------
+
+def learned_leg(args, dev):
+    """Train the codec on propagator snapshots of seeded random 192^3 models
+    (untimed), then time one RTM shot of the 384^3 smooth-model workload
+    (3000 steps, imaging every 4) with checkpoint recompute (every 50 steps)
+    and with learned storage, and compare the two images."""
+    import torch
+
+    import paper_1603_03971_gb300 as rtm
+    import rtm_inputs
+    from paper_1603_03971_gb300 import learned
+
+    t0 = time.perf_counter()
+    data = learned.training_snapshots(n_models=args.learned_models, size=192, nt=1200, every=40,
+                                      first=40, device=dev)
+    P, losses = learned.train(data, steps=args.learned_train_steps, batch=4, lr=1e-3,
+                              lr_min=5e-5, log_every=0)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    n_snap = int(data.shape[0])
+    del data
+    w = rtm_inputs.WORKLOADS["learned_384"]
+    v = w.velocity_model(device=dev).contiguous()
+    rec = torch.from_numpy(w.receivers()).to(dev)
+    pc = rtm.params_for(w, storage="ckpt", ckpt_every=50)
+    ws = rtm.alloc_workspace(pc, dev)
+    c = rtm.model_prep(pc, v, ws)
+    dobs = torch.empty((w.nt, pc.nrec), dtype=torch.float32, device=dev)
+    rtm.forward(pc, c, rec, ws, data=dobs)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    img_c = torch.zeros((w.nz, w.ny, w.nx), dtype=torch.float32, device=dev)
+    rtm.shot(pc, c, rec, dobs, ws, img_c)  # warm-up
+    img_c.zero_()
+    torch.cuda.synchronize()
+    e0.record()
+    rtm.shot(pc, c, rec, dobs, ws, img_c)
+    e1.record()
+    torch.cuda.synchronize()
+    t_ckpt = e0.elapsed_time(e1) / 1e3
+    del ws
+    pl = rtm.params_for(w, storage="learned")
+    wl = rtm.alloc_workspace(pl, dev)
+    img_l = torch.zeros_like(img_c)
+    rtm.shot_learned(pl, c, rec, dobs, P, wl, img_l)  # warm-up
+    img_l.zero_()
+    torch.cuda.synchronize()
+    e0.record()
+    rtm.shot_learned(pl, c, rec, dobs, P, wl, img_l)
+    e1.record()
+    torch.cuda.synchronize()
+    t_learned = e0.elapsed_time(e1) / 1e3
+    rtm.check(wl)
+    err = float((img_l - img_c).norm() / img_c.norm())
+    err_deep = float((img_l[16:] - img_c[16:]).norm() / img_c[16:].norm())
+    NZ, NY, NX = w.padded_shape
+    return {
+        "workload": "learned_384: 384^3 model (448^3 padded), r=4, 3000 steps, smooth random "
+                    "velocity, imaging every 4 steps (750 snapshots)",
+        "shot_s_checkpoint": t_ckpt, "checkpoint_every": 50,
+        "shot_s_learned": t_learned, "speedup_vs_checkpoint": t_ckpt / t_learned,
+        "image_rel_l2_vs_checkpoint": err, "target_rel_l2": 1e-2,
+        "image_rel_l2_below_z16": err_deep,
+        "compression": "8x (float32 snapshot -> 16 bfloat16 channels per 4^3 voxels)",
+        "train": {"models": args.learned_models, "snapshots": n_snap,
+                  "steps": args.learned_train_steps, "batch": 4, "seconds": train_s,
+                  "final_loss": losses[-1][1]},
+        "updates_per_shot_learned": 2 * w.nt * NX * NY * NZ,
+    }
+
+
+def batch_leg(args, dev):
+    """32 shots on seeded uneven apertures of a 1024 x 1024 x 512 layered /
+    salt model, radius-8 stencil, each a full checkpointed RTM, in one
+    persistent launch per wave inside one CUDA graph."""
+    import torch
+
+    import paper_1603_03971_gb300 as rtm
+    import rtm_inputs
+    from paper_1603_03971_gb300 import batch as B
+
+    cfg = rtm_inputs.BATCH_WORKLOAD
+    nz, ny, nx = cfg["model_shape"]
+    nt = args.batch_nt
+    vel = torch.from_numpy(rtm_inputs.layered_salt_velocity(nx, ny, nz, seed=cfg["seed"])).to(dev)
+    origin, size = rtm_inputs.batch_apertures(cfg["nshots"], (nz, ny, nx), seed=cfg["seed"])
+    aps = [B.Aperture(int(o[0]), int(o[1]), int(o[2]), int(s[0]), int(s[1]), int(s[2]),
+                      int(s[0]) // 2, int(s[1]) // 2, 4, 2) for o, s in zip(origin, size)]
+    dt = rtm_inputs.courant_dt(cfg["dx"], cfg["vmax"])
+    p = rtm.make_params(nx, ny, nz, cfg["nb"], cfg["radius"], nt, cfg["dx"], dt, cfg["f0"],
+                        1.0 / cfg["f0"], (0, 0, 0), 0, storage="ckpt", ckpt_every=50)
+    budget = 200 * 10 ** 9
+    ws = B.alloc_workspace(p, aps, budget, device=dev)
+    dobs = torch.zeros(B.data_size(p, aps), dtype=torch.float32, device=dev)
+    img = torch.zeros((nz, ny, nx), dtype=torch.float32, device=dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    B.run(p, aps, vel, dobs, img, ws, budget=budget)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    rtm.check(ws)
+    pts = sum((a.nx + 2 * p.nb) * (a.ny + 2 * p.nb) * (a.nz + 2 * p.nb) for a in aps)
+    updates = 3 * nt * pts
+    return {"workload": "32 shots, apertures 128-384 x 128-384 x 256-512 of a 1024x1024x512 "
+                        "layered/salt model, r=8, %d steps, checkpoint every 50" % nt,
+            "seconds": t, "gpoint_updates_per_s": updates / t / 1e9, "updates": updates,
+            "workspace_gb": ws.numel() / 1e9}
+
+
+# ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
 
@@ -262,11 +386,14 @@ def run_ours(args):
     w = workload(args)
     cfg = config_of(w)
     NZ, NY, NX = w.padded_shape
+    rtm.set_tuning(w.radius, 0, args.variant)
+    cfg["stencil_variant"] = args.variant
     src = shots.shot_source(rank, world, w.nx, w.ny, w.src[2]) if world > 1 else w.src
     p = rtm.params_for(w, src=src)
     rec_np = w.receivers()
     rec = torch.from_numpy(rec_np).to(dev)
     vel = w.velocity_model(device=dev).contiguous()
+    vel64 = vel.double().cpu().numpy() if (rank == 0 and world == 1) else None
     ws = rtm.alloc_workspace(p, dev, host_io=True)
     c = rtm.model_prep(p, vel, ws)
 
@@ -350,11 +477,22 @@ def run_ours(args):
 
     if world > 1:
         shots.stack_images(image)  # the multi-shot stack (outside the timed region)
+    del vel
+    learned = None
+    if rank == 0 and not args.no_learned:
+        del ws
+        torch.cuda.empty_cache()
+        learned = learned_leg(args, dev)
+        ws = None
+    batch_res = None
+    if rank == 0 and args.batch:
+        ws = None
+        torch.cuda.empty_cache()
+        batch_res = batch_leg(args, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        vel64 = vel.double().cpu().numpy()
-        del ws
+        ws = None
         torch.cuda.empty_cache()
         steps = 10 if NX * NY * NZ > 50_000_000 else 50
         s, u, threads = oracle_sample(w, vel64, steps)
@@ -370,7 +508,7 @@ def run_ours(args):
             "data": "synthetic (seeded smooth random velocity; observed data modelled on it)",
             "config": cfg, "shot_s": t_max / args.steps, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": st["launches"],
-            "clocks": clocks, "impl": "ours",
+            "clocks": clocks, "impl": "ours", "learned": learned, "batch": batch_res,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -289,6 +289,14 @@ typedef struct {
 } rtm_aperture;
 size_t rtm_batch_workspace_size(const rtm_params *p, int32_t nshots, const rtm_aperture *h_shots,
                                 size_t budget_bytes);
+/* Bound (seconds of SM clock at its base rate, default 20) of every
+ * inter-block wait of the persistent batch kernel. A wait that runs out sets
+ * an abort flag that every block sees, the launch ends without hanging, the
+ * status word reads RTM_ERR_TIMEOUT (rtm_check) and rtm_batch returns it.
+ * poison_shot >= 0 makes that shot's first work item wait for a count that
+ * is never reached: a host-injected failure for testing the timeout path
+ * (-1: off). */
+rtm_status rtm_batch_set_wait(double seconds, int32_t poison_shot);
 rtm_status rtm_batch(const rtm_params *p, int32_t nshots, const rtm_aperture *h_shots,
                      const float *d_vel, const float *d_dobs, float *d_data, float *d_image,
                      void *d_ws, size_t ws_bytes, size_t budget_bytes, int32_t zchunk,
@@ -328,8 +336,10 @@ rtm_status rtm_forward_noalloc(const rtm_params *p, const float *d_c, const int3
                                float *d_data, float *d_u_last, rtm_stream stream);
 
 /* Stencil tuning: z extent of the slab one thread block marches through
- * (0 = automatic) and the plane-load path (0 = automatic, 1 = vector loads
- * through registers, 2 = TMA). Applies to later calls on every thread. */
+ * (0 = automatic) and the plane-load path (0 = automatic: TMA where the
+ * driver provides tensor maps; 1 = 16-byte vector loads through registers;
+ * 2 = TMA bulk tensor copies into shared-memory rings). Applies to later
+ * calls on every thread. */
 rtm_status rtm_set_tuning(int32_t radius, int32_t zchunk, int32_t variant);
 
 /* Enable (1) or disable (0) per-launch CUDA-event timing of the stencil

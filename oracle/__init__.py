@@ -234,15 +234,22 @@ class Grid:
     """Padded grid with its coefficient ``c = v^2 dt^2`` and sponge."""
 
     def __init__(self, c: np.ndarray, nb: int, r: int, dx: float,
-                 sponge: bool = True):
+                 sponge: bool = True, profiles=None):
+        """``profiles = (gx, gy, gz)`` overrides the sponge profiles (a crop of
+        a larger grid keeps the profiles of the grid it was cut from)."""
         self.c = np.ascontiguousarray(c, dtype=np.float64)
         self.NZ, self.NY, self.NX = self.c.shape
         self.nb, self.r, self.dx = int(nb), int(r), float(dx)
         self.a = np.ascontiguousarray(coefficients(r))
         nbs = self.nb if sponge else 0
-        self.gx = sponge_profile(self.NX, nbs)
-        self.gy = sponge_profile(self.NY, nbs)
-        self.gz = sponge_profile(self.NZ, nbs)
+        if profiles is None:
+            self.gx = sponge_profile(self.NX, nbs)
+            self.gy = sponge_profile(self.NY, nbs)
+            self.gz = sponge_profile(self.NZ, nbs)
+        else:
+            self.gx, self.gy, self.gz = (np.ascontiguousarray(g, dtype=np.float64)
+                                         for g in profiles)
+            assert (self.gx.size, self.gy.size, self.gz.size) == (self.NX, self.NY, self.NZ)
         self._s = _Grid(self.NX, self.NY, self.NZ, self.nb, self.r, self.dx,
                         _ptr(self.a), _ptr(self.c), _ptr(self.gx), _ptr(self.gy),
                         _ptr(self.gz))

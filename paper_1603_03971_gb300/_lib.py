@@ -85,6 +85,7 @@ SIGNATURES = {
     "rtm_shot_learned": (ctypes.c_int, [_P, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _vp]),
     "rtm_snapshot": (ctypes.c_int, [_P, _vp, _sz, _i32, _vp, _vp]),
     "rtm_batch_workspace_size": (_sz, [_P, _i32, _vp, _sz]),
+    "rtm_batch_set_wait": (ctypes.c_int, [ctypes.c_double, _i32]),
     "rtm_batch": (ctypes.c_int, [_P, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _sz, _i32, _vp]),
     "rtm_ae_param_count": (_sz, []),
     "rtm_ae_workspace_size": (_sz, [_i32, _i32, _i32]),

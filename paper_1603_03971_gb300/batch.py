@@ -57,3 +57,9 @@ def run(p: RtmParams, apertures, vel: torch.Tensor, dobs: torch.Tensor, image: t
          ctypes.c_size_t(ws.numel()), ctypes.c_size_t(budget), int(zchunk),
          ctypes.c_void_p(s.cuda_stream))
     return image
+
+
+def set_wait(seconds: float = 20.0, poison_shot: int = -1):
+    """Bound of the persistent kernel's inter-block waits; ``poison_shot``
+    injects a wait that never completes (failure-path testing)."""
+    call("rtm_batch_set_wait", ctypes.c_double(seconds), int(poison_shot))

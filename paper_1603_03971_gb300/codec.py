@@ -106,3 +106,37 @@ def gemm_bf16(A: torch.Tensor, B: torch.Tensor, status=None, stream=None) -> tor
          _p(B.contiguous(), torch.bfloat16, "B"), _p(C), M, K, N,
          _p(status, torch.int32, "status"), _s(stream))
     return C
+
+
+def _time_codec(n: int, reps: int = 10, seed: int = 0):
+    """Encode and decode of a random n^3 snapshot; returns (encode ms, decode ms)."""
+    import numpy as np
+
+    import rtm_inputs
+
+    P = torch.from_numpy(rtm_inputs.ae_flat(rtm_inputs.ae_init_params(seed)).astype(np.float32))
+    P = P.cuda()
+    s = torch.randn(n, n, n, device="cuda")
+    ws = alloc_workspace((n, n, n))
+    lat, sc = encode(P, s, ws)
+    r = decode(P, lat, sc, ws)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record()
+    for _ in range(reps):
+        encode(P, s, ws, latent=lat, scale=sc)
+    e[1].record()
+    for _ in range(reps):
+        decode(P, lat, sc, ws, out=r)
+    e[2].record()
+    torch.cuda.synchronize()
+    return e[0].elapsed_time(e[1]) / reps, e[1].elapsed_time(e[2]) / reps
+
+
+if __name__ == "__main__":
+    import sys
+
+    n = int(sys.argv[1]) if len(sys.argv) > 1 else 384
+    reps = int(sys.argv[2]) if len(sys.argv) > 2 else 10
+    enc, dec = _time_codec(n, reps)
+    print("codec %d^3: encode %.3f ms, decode %.3f ms" % (n, enc, dec))

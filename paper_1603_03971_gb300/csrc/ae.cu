@@ -337,7 +337,25 @@ struct OpD12 {
                                       int tid) {
         OpD1::load_async(a.d1, m0, ch, sA, sB, tid);
     }
+    // W4 rounded to bfloat16, staged once per CTA
+    static constexpr int kExtraSmem = 256 * 4;
+    __device__ static void load_extra(const Args& a, uint8_t* extra, int tid) {
+        float* w = reinterpret_cast<float*>(extra);
+        for (int i = tid; i < 256; i += 128)
+            w[i] = __bfloat162float(__float2bfloat16_rn(a.d1.P[kOW4 + i]));
+    }
+    __device__ static void epilogue_x(const Args& a, int m0, int row, const float* acc,
+                                      const uint8_t* extra) {
+        epilogue_w(a, m0, row, acc, reinterpret_cast<const float*>(extra));
+    }
     __device__ static void epilogue(const Args& a, int m0, int row, const float* acc) {
+        float w4[256];
+        for (int i = 0; i < 256; i++)
+            w4[i] = __bfloat162float(__float2bfloat16_rn(a.d1.P[kOW4 + i]));
+        epilogue_w(a, m0, row, acc, w4);
+    }
+    __device__ static void epilogue_w(const Args& a, int m0, int row, const float* acc,
+                                      const float* w4) {
         const D1Args& d = a.d1;
         const long long v = m0 + row;
         if (v >= (long long)d.l.nx * d.l.ny * d.l.nz) return;
@@ -355,8 +373,7 @@ struct OpD12 {
         for (int e = 0; e < 8; e++) {
             float yv = 0.f;
 #pragma unroll
-            for (int c = 0; c < 32; c++)
-                yv = fmaf(__bfloat162float(__float2bfloat16_rn(d.P[kOW4 + e * 32 + c])), g[c], yv);
+            for (int c = 0; c < 32; c++) yv = fmaf(w4[e * 32 + c], g[c], yv);
             const int ez = e >> 2, ey = (e >> 1) & 1, ex = e & 1;
             a.out.p[(long long)(2 * gz + ez) * a.out.sz + (long long)(2 * gy + ey) * a.out.sy +
                     2 * gx + ex] = sc * (yv + b);
@@ -708,18 +725,30 @@ struct OpD1w {  // dW3[o][k][i] += sum_j ga3[2j + q][o] lat[j + t][i], class q =
 // ============================================================================
 // CUDA-core kernels
 // ============================================================================
+// sum of squares of a strided volume: rows of x, one row per block iteration,
+// float partials per thread, a block reduction in double, one atomic per block
 __global__ void k_sumsq(Vol in, double* acc) {
-    const long long n = (long long)in.nx * in.ny * in.nz;
-    double s = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        int x, y, z;
-        decode3(i, in.nx, in.ny, x, y, z);
-        const double v = in.p[(long long)z * in.sz + (long long)y * in.sy + x];
-        s += v * v;
+    const long long rows = (long long)in.ny * in.nz;
+    float s = 0.f;
+    for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int y = (int)(r % in.ny), z = (int)(r / in.ny);
+        const float* row = in.p + (long long)z * in.sz + (long long)y * in.sy;
+        for (int x = threadIdx.x; x < in.nx; x += blockDim.x) {
+            const float v = __ldg(row + x);
+            s = fmaf(v, v, s);
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(acc, s);
+    double d = s;
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    __shared__ double part[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) part[wid] = d;
+    __syncthreads();
+    if (wid == 0) {
+        double t = lane < (int)(blockDim.x >> 5) ? part[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) atomicAdd(acc, t);
+    }
 }
 
 __global__ void k_scale(const double* acc, long long n, float* sigma, float* inv_sigma) {
@@ -861,9 +890,9 @@ cudaError_t ae_rms(const Vol& in, AeScalars* sc, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(&sc->sumsq, 0, sizeof(double), s);
     if (e != cudaSuccess) return e;
     const long long n = (long long)in.nx * in.ny * in.nz;
-    long long blocks = (n + 255) / 256;
+    long long blocks = (long long)in.ny * in.nz;
     if (blocks > 152 * 8) blocks = 152 * 8;
-    k_sumsq<<<(unsigned)blocks, 256, 0, s>>>(in, &sc->sumsq);
+    k_sumsq<<<(unsigned)blocks, 128, 0, s>>>(in, &sc->sumsq);
     k_scale<<<1, 1, 0, s>>>(&sc->sumsq, n, &sc->sigma, &sc->inv_sigma);
     return cudaGetLastError();
 }

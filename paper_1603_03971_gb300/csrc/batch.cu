@@ -276,7 +276,8 @@ __global__ void __launch_bounds__(256, R == 4 ? 2 : 1) k_batch(const __grid_cons
         const BatchShot& S = A.shots[s];
         const int tile = (int)(r - S.item_base);
         if (tid == 0) {
-            const unsigned int target = (unsigned int)t * (unsigned int)S.ntiles;
+            unsigned int target = (unsigned int)t * (unsigned int)S.ntiles;
+            if (s == A.poison_shot && t == 0 && tile == 0) target = 0xFFFFFFFFu;  // failure test
             s_go = wait_counter(A.ctrl, &A.ctrl->done[s], target, A.timeout_cycles, A.status) ? 1
                                                                                          : 0;
         }

@@ -16,6 +16,8 @@ using namespace rtm;
 namespace {
 
 constexpr size_t kAlB = 256;
+double g_wait_seconds = 20.0;  // bound of each inter-block wait
+int g_poison_shot = -1;
 constexpr int kMaxShotsTotal = 1024;
 size_t upb(size_t v) { return (v + kAlB - 1) / kAlB * kAlB; }
 
@@ -161,6 +163,14 @@ Plan make_plan(const rtm_params* p, int nshots, const rtm_aperture* sh, size_t b
 
 extern "C" {
 
+rtm_status rtm_batch_set_wait(double seconds, int32_t poison_shot) {
+    if (!(seconds > 0.0) || seconds > 3600.0)
+        return (rtm_status)set_error(RTM_ERR_INVALID, "wait bound %g s out of (0, 3600]", seconds);
+    g_wait_seconds = seconds;
+    g_poison_shot = poison_shot;
+    return RTM_OK;
+}
+
 size_t rtm_batch_workspace_size(const rtm_params* p, int32_t nshots, const rtm_aperture* h_shots,
                                 size_t budget_bytes) {
     if (!p || check_batch(p, nshots, h_shots) != RTM_OK) return 0;
@@ -264,8 +274,9 @@ rtm_status rtm_batch(const rtm_params* p, int32_t nshots, const rtm_aperture* h_
     A.ckpt_every = p->ckpt_every;
     A.image_every = p->image_every;
     A.nt = p->nt;
-    A.timeout_cycles = (long long)clock_khz * 1000LL * 20;  // about 20 s at the base clock
+    A.timeout_cycles = (long long)((double)clock_khz * 1000.0 * g_wait_seconds);
     A.status = reinterpret_cast<int*>(ws);
+    A.poison_shot = g_poison_shot;
 
     // capture on a private stream (the caller's may be the legacy default
     // stream, which cannot be captured); the graph runs on the caller's stream
@@ -326,6 +337,12 @@ rtm_status rtm_batch(const rtm_params* p, int32_t nshots, const rtm_aperture* h_
     cudaGraphExecDestroy(exec);
     if (es != cudaSuccess)
         return (rtm_status)set_error(RTM_ERR_CUDA, "batch graph failed: %s", cudaGetErrorString(es));
+    int h_status = 0;
+    CUB(cudaMemcpy(&h_status, ws, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h_status == RTM_ERR_TIMEOUT)
+        return (rtm_status)set_error(RTM_ERR_TIMEOUT,
+                                     "a persistent-kernel wait ran out after %.3g s; the batch "
+                                     "was abandoned", g_wait_seconds);
     return RTM_OK;
 }
 

@@ -57,6 +57,7 @@ struct BatchArgs {
     int zchunk, ckpt_every, image_every, nt;
     long long timeout_cycles;
     int* status;  // workspace status word (RTM_ERR_TIMEOUT on a wait that ran out)
+    int poison_shot;  // >= 0: that shot's first item waits for a count nothing reaches
 };
 
 cudaError_t launch_batch(int radius, const BatchArgs& a, int grid, cudaStream_t s);

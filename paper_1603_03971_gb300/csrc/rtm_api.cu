@@ -322,7 +322,8 @@ rtm_status make_ctx(Ctx& C, const rtm_params* p, const float* c, void* ws, rtm_s
     C.base.zchunk = zc > 0 ? zc : auto_zchunk(p->radius, C.d.NX, C.d.NY, C.d.NZ);
     if ((C.d.NZ + C.base.zchunk - 1) / C.base.zchunk > 65535)
         C.base.zchunk = (C.d.NZ + 65534) / 65535;  // grid.z limit
-    C.variant = var;
+    // automatic: TMA plane loads wherever the driver provides tensor maps
+    C.variant = var != 0 ? var : (tma_available() ? 2 : 1);
     return RTM_OK;
 }
 
@@ -354,12 +355,14 @@ rtm_status stencil(Ctx& C, int mode, const float* cur, float* prev, float* snap,
     if (timing) {
         PendingTiming t{t_timer.get(), t_timer.get(), mode, stencil_bytes(C, mode)};
         CU(cudaEventRecord(t.a, C.s));
-        CU(launch_stencil(C.p->radius, mode, a, C.s));
+        CU(C.variant == 2 ? launch_stencil_tma(C.p->radius, mode, a, C.status(), C.s)
+                          : launch_stencil(C.p->radius, mode, a, C.s));
         CU(cudaEventRecord(t.b, C.s));
         t_timer.pending.push_back(t);
         if (t_timer.pending.size() >= 2048) CHECK(t_timer.drain(C.s));
     } else {
-        CU(launch_stencil(C.p->radius, mode, a, C.s));
+        CU(C.variant == 2 ? launch_stencil_tma(C.p->radius, mode, a, C.status(), C.s)
+                          : launch_stencil(C.p->radius, mode, a, C.s));
     }
     return RTM_OK;
 }

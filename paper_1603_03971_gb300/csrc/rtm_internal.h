@@ -41,6 +41,10 @@ struct StepArgs {
 };
 
 cudaError_t launch_stencil(int radius, int mode, const StepArgs& a, cudaStream_t s);
+// the same step with TMA plane loads (tuning variant 2); status: device status word
+cudaError_t launch_stencil_tma(int radius, int mode, const StepArgs& a, int* status,
+                               cudaStream_t s);
+bool tma_available();
 int auto_zchunk(int radius, int NX, int NY, int NZ);
 
 // ---- small kernels (aux.cu) -------------------------------------------------

@@ -1,0 +1,346 @@
+// Stencil step with TMA plane loads (tuning variant 2).
+//
+// The same leapfrog update and epilogues as k_stencil, with the plane loads
+// moved to the tensor memory accelerator: one thread issues 3D bulk tensor
+// copies of the next planes into shared-memory rings, R + P + 1 planes of
+// u^n (a 64 x 16 tile with its r-wide halo; cells outside the padded grid
+// arrive as zeros, the Dirichlet ghost cells) and P + 1 planes of the
+// pointwise operands (u^{n-1}, c, and the snapshot / accumulator of the
+// backward modes). Each ring slot has an mbarrier that the copy completes
+// (expect-tx); P = 2 planes are in flight ahead of the one being computed.
+// Each thread keeps the 2r + 1 column values of its 4-point vector in a
+// register queue, whose head it reads from the newest u^n plane in shared
+// memory. One block barrier per plane frees the slots for refilling.
+//
+// Tensor-map rules respected here: every row starts on a 16-byte boundary
+// (NX % 4 == 0), the x coordinate of every copy is a multiple of 4 floats
+// (x0 - r with x0 % 64 == 0, r % 4 == 0), boxes are at most 256 per side and
+// their rows a multiple of 16 bytes, and shared destinations are 128-byte
+// aligned. Copies only load; negative or out-of-range coordinates read zeros.
+
+#include <cuda.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "rtm_internal.h"
+#include "stencil_common.cuh"
+
+namespace rtm {
+
+namespace {
+
+constexpr int kPrefetch = 2;
+constexpr long long kTmaWaitLimit = 1LL << 26;
+
+struct TmaMaps {
+    CUtensorMap u, prev, c, e1, e2;
+};
+
+template <int R, int NA>
+struct TmaCfg {
+    using T = Tile<R>;
+    static constexpr int SU = R + kPrefetch + 1;
+    static constexpr int SA = kPrefetch + 1;
+    static constexpr int UPLANE = T::SH * T::SW;  // floats
+    static constexpr int APLANE = T::TY * T::TX;
+    static constexpr int SMEM = (SU * UPLANE + SA * NA * APLANE) * 4;
+};
+
+__device__ __forceinline__ uint32_t s_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void bar_init(uint64_t* b) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(b)));
+}
+__device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, int* abort_flag) {
+    if (*reinterpret_cast<volatile int*>(abort_flag)) return false;
+    const uint32_t a = s_u32(b);
+    for (long long i = 0; i < kTmaWaitLimit; i++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    *reinterpret_cast<volatile int*>(abort_flag) = 1;
+    return false;
+}
+__device__ __forceinline__ void tma3(float* dst, const CUtensorMap* map, int x, int y, int z,
+                                     uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(s_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(s_u32(bar))
+        : "memory");
+}
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(256, R == 4 ? 2 : 1)
+    k_stencil_tma(const __grid_constant__ StepArgs A, const __grid_constant__ TmaMaps M, int* status) {
+    using T = Tile<R>;
+    constexpr int NA = (MODE == MODE_BWD_IMAGE || MODE == MODE_BWD_GRAD) ? 4 : 2;
+    using C = TmaCfg<R, NA>;
+    extern __shared__ __align__(128) float dsm[];
+    float* uring = dsm;
+    float* aring = dsm + C::SU * C::UPLANE;
+    __shared__ __align__(8) uint64_t ubar[C::SU];
+    __shared__ __align__(8) uint64_t abar[C::SA];
+    __shared__ int abort_flag;
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * T::BX + tx;
+    const int x0 = blockIdx.x * T::TX, y0 = blockIdx.y * T::TY;
+    const int x = x0 + 4 * tx, y = y0 + ty;
+    const int zb = blockIdx.z * A.zchunk;
+    const int ze = min(A.NZ, zb + A.zchunk);
+    const bool own = x < A.NX && y < A.NY;
+    const size_t plane = (size_t)A.NX * (size_t)A.NY;
+    const size_t col = (size_t)y * A.NX + x;
+    const bool xm = (x + 3 >= A.nb) && (x < A.nb + A.nx);
+    const bool ym = (y >= A.nb) && (y < A.nb + A.ny);
+    const size_t slab_col = (size_t)(y - A.nb) * A.NX + x;
+    const size_t slab_plane = (size_t)A.ny * A.NX;
+
+    if (tid == 0) {
+        for (int s = 0; s < C::SU; s++) bar_init(&ubar[s]);
+        for (int s = 0; s < C::SA; s++) bar_init(&abar[s]);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    const int last_u = ze - 1 + R;  // newest u^n plane needed (queue head of the last step)
+    auto issue_u = [&](int p) {
+        const int slot = (p - zb) % C::SU;
+        bar_expect(&ubar[slot], C::UPLANE * 4);
+        tma3(uring + slot * C::UPLANE, &M.u, x0 - R, y0 - R, p, &ubar[slot]);
+    };
+    auto issue_a = [&](int p) {
+        const int slot = (p - zb) % C::SA;
+        float* base = aring + slot * NA * C::APLANE;
+        bar_expect(&abar[slot], NA * C::APLANE * 4);
+        tma3(base, &M.prev, x0, y0, p, &abar[slot]);
+        tma3(base + C::APLANE, &M.c, x0, y0, p, &abar[slot]);
+        if constexpr (MODE == MODE_BWD_IMAGE) {
+            tma3(base + 2 * C::APLANE, &M.e1, x0, y0 - A.nb, p - A.nb, &abar[slot]);
+            tma3(base + 3 * C::APLANE, &M.e2, x0, y0 - A.nb, p - A.nb, &abar[slot]);
+        } else if constexpr (MODE == MODE_BWD_GRAD) {
+            tma3(base + 2 * C::APLANE, &M.e1, x0, y0, p, &abar[slot]);
+            tma3(base + 3 * C::APLANE, &M.e2, x0, y0, p, &abar[slot]);
+        }
+    };
+    if (tid == 0) {
+        for (int p = zb; p < zb + R + kPrefetch && p <= last_u; p++) issue_u(p);
+        for (int p = zb; p < zb + kPrefetch && p < ze; p++) issue_a(p);
+    }
+
+    F4 gxy = zero4();
+    if (own) {
+        const float gyv = A.gy[y];
+#pragma unroll
+        for (int i = 0; i < 4; i++) gxy.v[i] = A.gx[x + i] * gyv;
+    }
+    // queue planes zb - R .. zb + R - 1 straight from global memory
+    F4 q[2 * R + 1];
+#pragma unroll
+    for (int i = 0; i < 2 * R; i++) {
+        const int zz = zb - R + i;
+        q[i] = (own && zz >= 0 && zz < A.NZ) ? ld_keep(A.u_cur + (size_t)zz * plane + col) : zero4();
+    }
+    q[2 * R] = zero4();
+
+    const int own_off = (R + ty) * T::SW + R + 4 * tx;  // this vector in a u^n plane
+    const int aux_off = ty * T::TX + 4 * tx;             // this vector in an aux plane
+
+    for (int z = zb; z < ze; z++) {
+        if (tid == 0 && !abort_flag) {
+            if (z + R + kPrefetch <= last_u) issue_u(z + R + kPrefetch);
+            if (z + kPrefetch < ze) issue_a(z + kPrefetch);
+        }
+        const int ph = z + R;  // queue head plane
+        const int sh = (ph - zb) % C::SU;
+        bool ok = bar_wait(&ubar[sh], (uint32_t)(((ph - zb) / C::SU) & 1), &abort_flag);
+        q[2 * R] = lds4(uring + sh * C::UPLANE + own_off);
+        const int sc = (z - zb) % C::SU;
+        ok = bar_wait(&ubar[sc], (uint32_t)(((z - zb) / C::SU) & 1), &abort_flag) && ok;
+        const int sa = (z - zb) % C::SA;
+        ok = bar_wait(&abar[sa], (uint32_t)(((z - zb) / C::SA) & 1), &abort_flag) && ok;
+        const float* S = uring + sc * C::UPLANE;
+        const float* aux = aring + sa * NA * C::APLANE;
+
+        if (own && ok) {
+            float v[4 + 2 * R];
+#pragma unroll
+            for (int h = 0; h < T::HX; h++) {
+                const F4 l = lds4(S + (R + ty) * T::SW + 4 * tx + 4 * h);
+                const F4 r = lds4(S + (R + ty) * T::SW + R + 4 * tx + 4 + 4 * h);
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    v[4 * h + i] = l.v[i];
+                    v[R + 4 + 4 * h + i] = r.v[i];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; i++) v[R + i] = q[R].v[i];
+            F4 lap;
+#pragma unroll
+            for (int i = 0; i < 4; i++) lap.v[i] = A.a[0] * q[R].v[i];
+#pragma unroll
+            for (int k = 1; k <= R; k++) {
+                const F4 ym_ = lds4(S + (R + ty - k) * T::SW + R + 4 * tx);
+                const F4 yp_ = lds4(S + (R + ty + k) * T::SW + R + 4 * tx);
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const float px = v[R + i - k] + v[R + i + k];
+                    const float py = ym_.v[i] + yp_.v[i];
+                    const float pz = q[R - k].v[i] + q[R + k].v[i];
+                    lap.v[i] = fmaf(A.a[k], (px + py) + pz, lap.v[i]);
+                }
+            }
+            const F4 up = lds4(aux + aux_off);
+            const F4 cc = lds4(aux + C::APLANE + aux_off);
+            const float gzv = A.gz[z];
+            F4 out;
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const float g = gxy.v[i] * gzv;
+                out.v[i] = g * fmaf(cc.v[i], lap.v[i], 2.0f * q[R].v[i]) - (g * g) * up.v[i];
+            }
+            const size_t o = (size_t)z * plane + col;
+            st_stream(A.u_prev + o, out);
+            if constexpr (MODE == MODE_FWD_SNAP) {
+                if (xm && ym && z >= A.nb && z < A.nb + A.nz)
+                    st_stream(A.snap + (size_t)(z - A.nb) * slab_plane + slab_col, out);
+            } else if constexpr (MODE == MODE_BWD_IMAGE) {
+                if (xm && ym && z >= A.nb && z < A.nb + A.nz) {
+                    const F4 sv = lds4(aux + 2 * C::APLANE + aux_off);
+                    F4 acc = lds4(aux + 3 * C::APLANE + aux_off);
+#pragma unroll
+                    for (int i = 0; i < 4; i++) acc.v[i] = fmaf(sv.v[i], out.v[i], acc.v[i]);
+                    st_stream(A.acc + (size_t)(z - A.nb) * slab_plane + slab_col, acc);
+                }
+            } else if constexpr (MODE == MODE_FWD_LU) {
+                st_stream(A.snap + o, lap);
+            } else if constexpr (MODE == MODE_BWD_GRAD) {
+                const F4 sv = lds4(aux + 2 * C::APLANE + aux_off);
+                F4 acc = lds4(aux + 3 * C::APLANE + aux_off);
+#pragma unroll
+                for (int i = 0; i < 4; i++) acc.v[i] = fmaf(out.v[i], sv.v[i], acc.v[i]);
+                st_stream(A.acc + o, acc);
+            }
+        }
+        __syncthreads();  // every thread is done with planes z (centre, aux): slots reusable
+#pragma unroll
+        for (int i = 0; i < 2 * R; i++) q[i] = q[i + 1];
+    }
+    // a slab shorter than r issued planes [ze, zb + r) that no step waited
+    // for: let those copies land before the block exits
+    if (tid == 0) {
+        for (int p = ze; p < zb + R && p <= last_u; p++)
+            bar_wait(&ubar[(p - zb) % C::SU], (uint32_t)(((p - zb) / C::SU) & 1), &abort_flag);
+        if (abort_flag && status) atomicCAS(status, 0, 5);  // RTM_ERR_TIMEOUT
+    }
+}
+
+// ---- host side: tensor maps ---------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+cudaError_t make_map(CUtensorMap* m, const float* base, int nx, int ny, int nz, int bx, int by) {
+    EncodeTiledFn f = encode_fn();
+    if (!f) return cudaErrorNotSupported;
+    if (((uintptr_t)base % 16) || (nx % 4)) return cudaErrorInvalidValue;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = f(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int R, int MODE>
+cudaError_t launch_tma_t(const StepArgs& a, int* status, cudaStream_t s) {
+    using T = Tile<R>;
+    constexpr int NA = (MODE == MODE_BWD_IMAGE || MODE == MODE_BWD_GRAD) ? 4 : 2;
+    constexpr int smem = TmaCfg<R, NA>::SMEM;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_stencil_tma<R, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    TmaMaps M;
+    memset(&M, 0, sizeof M);
+    cudaError_t e;
+    if ((e = make_map(&M.u, a.u_cur, a.NX, a.NY, a.NZ, T::TX + 2 * R, T::TY + 2 * R)) != cudaSuccess)
+        return e;
+    if ((e = make_map(&M.prev, a.u_prev, a.NX, a.NY, a.NZ, T::TX, T::TY)) != cudaSuccess) return e;
+    if ((e = make_map(&M.c, a.c, a.NX, a.NY, a.NZ, T::TX, T::TY)) != cudaSuccess) return e;
+    if (MODE == MODE_BWD_IMAGE) {
+        if ((e = make_map(&M.e1, a.snap, a.NX, a.ny, a.nz, T::TX, T::TY)) != cudaSuccess) return e;
+        if ((e = make_map(&M.e2, a.acc, a.NX, a.ny, a.nz, T::TX, T::TY)) != cudaSuccess) return e;
+    } else if (MODE == MODE_BWD_GRAD) {
+        if ((e = make_map(&M.e1, a.snap, a.NX, a.NY, a.NZ, T::TX, T::TY)) != cudaSuccess) return e;
+        if ((e = make_map(&M.e2, a.acc, a.NX, a.NY, a.NZ, T::TX, T::TY)) != cudaSuccess) return e;
+    }
+    dim3 block(T::BX, T::BY);
+    dim3 grid((a.NX + T::TX - 1) / T::TX, (a.NY + T::TY - 1) / T::TY,
+              (a.NZ + a.zchunk - 1) / a.zchunk);
+    k_stencil_tma<R, MODE><<<grid, block, smem, s>>>(a, M, status);
+    return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t launch_tma_r(int mode, const StepArgs& a, int* status, cudaStream_t s) {
+    switch (mode) {
+        case MODE_FWD: return launch_tma_t<R, MODE_FWD>(a, status, s);
+        case MODE_FWD_SNAP: return launch_tma_t<R, MODE_FWD_SNAP>(a, status, s);
+        case MODE_BWD_IMAGE: return launch_tma_t<R, MODE_BWD_IMAGE>(a, status, s);
+        case MODE_FWD_LU: return launch_tma_t<R, MODE_FWD_LU>(a, status, s);
+        case MODE_BWD_GRAD: return launch_tma_t<R, MODE_BWD_GRAD>(a, status, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+bool tma_available() { return encode_fn() != nullptr; }
+
+cudaError_t launch_stencil_tma(int radius, int mode, const StepArgs& a, int* status,
+                               cudaStream_t s) {
+    if (a.zchunk < 1) return cudaErrorInvalidValue;
+    switch (radius) {
+        case 4: return launch_tma_r<4>(mode, a, status, s);
+        case 8: return launch_tma_r<8>(mode, a, status, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace rtm

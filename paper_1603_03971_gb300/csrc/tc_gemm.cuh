@@ -25,6 +25,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace rtm {
 namespace tc {
 
@@ -37,6 +39,18 @@ constexpr int kStageBytes = kABytes + kBBytes;
 constexpr int kTmemCols = 32;
 constexpr long long kWaitLimit = 1LL << 24;  // mbarrier polls before giving up
 constexpr int kErrTimeout = 5;                // == RTM_ERR_TIMEOUT
+
+// optional per-op extra shared memory (filled once per CTA by Op::load_extra
+// and handed to Op::epilogue_x)
+template <class Op, class = void>
+struct extra_smem {
+    static constexpr int value = 0;
+};
+template <class Op>
+struct extra_smem<Op, std::void_t<decltype(Op::kExtraSmem)>> {
+    static constexpr int value = Op::kExtraSmem;
+};
+
 
 // byte offset of element (r, k) in a K-major no-swizzle slab (K width 32)
 __device__ __forceinline__ uint32_t kmajor_off(int r, int k) {
@@ -274,7 +288,9 @@ __global__ void __launch_bounds__(128) k_tc_gemm_async(const __grid_constant__ t
     constexpr int N = Op::N;
     constexpr int S = kAsyncStages;
     static_assert(N == 16 || N == 32, "N must be 16 or 32");
+    constexpr int L = S - 2;  // slabs loaded ahead; a stage is refilled two MMAs after its use
     __shared__ __align__(1024) uint8_t smem[S][kStageBytes];
+    __shared__ __align__(16) uint8_t extra[extra_smem<Op>::value > 0 ? extra_smem<Op>::value : 16];
     __shared__ __align__(8) uint64_t bars[S];
     __shared__ uint32_t tmem_slot;
 
@@ -288,29 +304,31 @@ __global__ void __launch_bounds__(128) k_tc_gemm_async(const __grid_constant__ t
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) tmem_alloc(&tmem_slot, kTmemCols);
+    if constexpr (extra_smem<Op>::value > 0) Op::load_extra(args, extra, tid);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     constexpr uint32_t idesc = idesc_bf16(kRows, N);
 
-    for (int c = 0; c < S - 1; c++) {
+    for (int c = 0; c < L; c++) {
         if (c < nch) Op::load_async(args, m0, c0 + c, smem[c], smem[c] + kABytes, tid);
         cp_async_commit();
     }
     bool ok = true;
     int issued = 0;
     for (int i = 0; i < nch && ok; i++) {
-        const int j = i + S - 1;
+        const int j = i + L;
         if (j < nch) {
-            // slab j reuses the stage of slab i - 1
-            if (i >= 1) ok = mbar_wait(&bars[(i - 1) % S], (uint32_t)(((i - 1) / S) & 1));
+            // slab j reuses the stage of slab j - S = i - 2, whose MMAs were
+            // issued two iterations ago
+            if (j >= S) ok = mbar_wait(&bars[(j - S) % S], (uint32_t)(((j - S) / S) & 1));
             ok = __syncthreads_and(ok);
             if (!ok) break;
             Op::load_async(args, m0, c0 + j, smem[j % S], smem[j % S] + kABytes, tid);
         }
         cp_async_commit();
-        cp_async_wait<S - 1>();
+        cp_async_wait<L>();
         fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
@@ -345,8 +363,12 @@ __global__ void __launch_bounds__(128) k_tc_gemm_async(const __grid_constant__ t
 #pragma unroll
         for (int n = 0; n < N; n++) acc[n] = 0.0f;
     }
-    if (ok) Op::epilogue(args, m0, tid, acc);
-    else if (tid == 0 && status) atomicCAS(status, 0, kErrTimeout);
+    if (ok) {
+        if constexpr (extra_smem<Op>::value > 0) Op::epilogue_x(args, m0, tid, acc, extra);
+        else Op::epilogue(args, m0, tid, acc);
+    } else if (tid == 0 && status) {
+        atomicCAS(status, 0, kErrTimeout);
+    }
 
     tc_fence_before();
     __syncthreads();

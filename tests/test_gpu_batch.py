@@ -108,3 +108,27 @@ def test_batch_rejects_bad_apertures_on_the_host():
     arr = (batch.Aperture * 1)(*bad)
     assert _lib.lib().rtm_batch_workspace_size(ctypes.byref(p), 1, arr, 0) == 0
     del rtm
+
+
+def test_batch_wait_timeout_is_reported_not_hung():
+    """A host-injected wait that nothing completes runs out after about a
+    second: rtm_batch returns RTM_ERR_TIMEOUT, the device stays usable and
+    the next batch is correct."""
+    import time
+
+    import paper_1603_03971_gb300 as rtm
+    from paper_1603_03971_gb300 import batch
+
+    p, vel, dobs = _setup(4, 12, 6, 1)
+    batch.set_wait(1.0, poison_shot=1)
+    try:
+        t0 = time.time()
+        with pytest.raises(rtm.RtmError) as e:
+            _run(p, vel, dobs)
+        assert e.value.code == 5
+        assert time.time() - t0 < 60
+    finally:
+        batch.set_wait(20.0, -1)
+    img, _ = _run(p, vel, dobs)
+    ref, _ = _oracle(p, vel, dobs)
+    assert rel_l2(img, ref) <= TOL

@@ -366,3 +366,28 @@ def _misfit_at(p, v2, d_obs):
     q = oracle.Problem(v2, p.nb, p.r, p.dx, p.dt, p.nt, p.f0, p.t0, (10, 9, 4),
                        rtm_inputs.surface_receivers(20, 18, 2, stride=3), squared=True)
     return q.misfit(d_obs)
+
+
+def test_crop_with_the_grids_profiles_reproduces_the_full_grid():
+    """After n steps the discrete field vanishes beyond n r cells of the
+    source, so a crop with that margin that keeps the full grid's c and sponge
+    profiles reproduces the full-grid field exactly (used by the full-size
+    sampled parity tests)."""
+    r, nb, n_model, dx = 4, 10, 40, 10.0
+    vel = rtm_inputs.smooth_random_velocity(n_model, n_model, n_model, 3.0, 1500.0, 3000.0, 5)
+    dt = rtm_inputs.courant_dt(dx, 3000.0)
+    nt = 6
+    src = (20, 22, 3)
+    full = oracle.Problem(vel, nb, r, dx, dt, nt, 30.0, 0.03, src, np.array([[20, 22, 5]]))
+    ref = full.forward(keep_last=True)["last"][1]
+    sz, sy, sx = (src[2] + nb, src[1] + nb, src[0] + nb)
+    m = nt * r + 1
+    z0, z1 = max(0, sz - m), min(full.grid.NZ, sz + m + 1)
+    y0, y1 = max(0, sy - m), min(full.grid.NY, sy + m + 1)
+    x0, x1 = max(0, sx - m), min(full.grid.NX, sx + m + 1)
+    g = oracle.Grid(full.grid.c[z0:z1, y0:y1, x0:x1], nb, r, dx,
+                    profiles=(full.grid.gx[x0:x1], full.grid.gy[y0:y1], full.grid.gz[z0:z1]))
+    s_lin = ((sz - z0) * (y1 - y0) + (sy - y0)) * (x1 - x0) + (sx - x0)
+    out = g.forward(full.w, s_lin, np.array([s_lin]), keep_last=True)["last"][1]
+    np.testing.assert_array_equal(out, ref[z0:z1, y0:y1, x0:x1])
+    assert np.abs(ref).sum() == pytest.approx(np.abs(out).sum(), rel=1e-14)
