@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="smooth_512")
     ap.add_argument("--nt", type=int, default=0, help="override the step count (testing only)")
+    ap.add_argument("--model", type=int, default=0,
+                    help="override the model edge (profiling cases; the line is then not the "
+                         "headline workload)")
+    ap.add_argument("--ckpt-every", type=int, default=0, help="override the checkpoint interval")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-steps", type=int, default=2,
@@ -75,6 +79,11 @@ def workload(args):
     w = rtm_inputs.WORKLOADS[args.workload]
     if args.nt:
         w = w.scaled(nt=args.nt)
+    if args.model:
+        n = args.model
+        w = w.scaled(nx=n, ny=n, nz=n, src=(n // 2, n // 2, w.src[2]), name=w.name + "@%d" % n)
+    if args.ckpt_every:
+        w = w.scaled(ckpt_every=args.ckpt_every)
     return w
 
 

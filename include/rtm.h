@@ -255,6 +255,14 @@ rtm_status rtm_ae_train_step(float *d_params, float *d_adam_m, float *d_adam_v, 
                              float lr, const float *d_batch, int32_t batch, int32_t nx,
                              int32_t ny, int32_t nz, double *d_loss, float *d_grad, void *d_ws,
                              size_t ws_bytes, rtm_stream stream);
+/* Inference decoder used by rtm_ae_decode and the learned-storage backward
+ * pass: 0 automatic (the z-marching kernel: latent planes loaded by TMA and
+ * read in place by the tensor cores, D1 and D2 fused, one persistent CTA per
+ * SM; the GEMM-engine decoder when the driver has no tensor-map encoder),
+ * 1 the GEMM-engine decoder, 2 the z-marching kernel where it can run.
+ * Both give the same values. Process-wide; returns RTM_ERR_INVALID for other
+ * values. */
+rtm_status rtm_ae_set_decoder(int32_t which);
 /* The tensor-core engine under the codec, exposed for checking: C[M][N] =
  * A[M][K] * B[N][K]^T, bfloat16 in, float32 out, K a multiple of 32, N 16 or
  * 32. A bounded wait that runs out writes RTM_ERR_TIMEOUT to *d_status. */

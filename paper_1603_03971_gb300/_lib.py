@@ -96,6 +96,7 @@ SIGNATURES = {
     "rtm_ae_train_step": (ctypes.c_int, [_vp, _vp, _vp, _i32, ctypes.c_float, _vp, _i32, _i32,
                                          _i32, _i32, _vp, _vp, _vp, _sz, _vp]),
     "rtm_ae_gemm_bf16": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
+    "rtm_ae_set_decoder": (ctypes.c_int, [_i32]),
     "rtm_set_timing": (ctypes.c_int, [_i32]),
     "rtm_stats_get": (ctypes.c_int, [ctypes.POINTER(RtmStats)]),
     "rtm_stats_reset": (ctypes.c_int, []),

@@ -108,6 +108,14 @@ def gemm_bf16(A: torch.Tensor, B: torch.Tensor, status=None, stream=None) -> tor
     return C
 
 
+def set_decoder(which: str = "auto") -> None:
+    """Inference decoder: "auto", "gemm" (GEMM-engine decoder) or "march"
+    (z-marching kernel with TMA plane loads read in place by the tensor
+    cores). Both give the same values."""
+    code = {"auto": 0, "gemm": 1, "march": 2}[which]
+    call("rtm_ae_set_decoder", code)
+
+
 def _time_codec(n: int, reps: int = 10, seed: int = 0):
     """Encode and decode of a random n^3 snapshot; returns (encode ms, decode ms)."""
     import numpy as np

@@ -925,6 +925,9 @@ cudaError_t ae_decode(const float* P, const bf16* lat, const float* sigma, const
         return run<OpD2>(a2, dim3(tiles((long long)h.nx * h.ny * h.nz)), status, s);
     }
     D12Args a{D1Args{lat, l, P, nullptr, h}, sigma, out};
+    const cudaError_t e = ae_decode_march(a, status, s);
+    if (e != cudaErrorNotSupported) return e;
+    cudaGetLastError();
     return run_async<OpD12>(a, dim3(tiles((long long)l.nx * l.ny * l.nz), 8), status, s);
 }
 

@@ -1,0 +1,435 @@
+// Inference decoder, z-marching: D1 (transposed conv 16 -> 32, kernel 4,
+// stride 2, padding 1) + LeakyReLU + D2 (transposed patch conv 32 -> 1) in one
+// persistent kernel, one CTA per SM.
+//
+// Work item: a column of 8 x 16 latent voxels (x, y) over a range of z. For
+// each latent plane z the 128 voxels of the column are the M = 128 rows of
+// 8 parities x 8 taps = 64 tcgen05.mma (K = 16 input channels each, N = 32
+// output channels), accumulated per parity into tensor memory.
+//
+// The A operands are never gathered. TMA copies each latent plane of the
+// column with a one-voxel halo (10 x 18 voxels, zeros outside the grid) into
+// a shared-memory ring as two 8-channel halves of [18][10] 16-byte rows: that
+// is the canonical K-major no-swizzle layout of a 128-row operand whose 8-row
+// groups are y rows (stride 160 B) and whose two K core matrices are the two
+// channel halves. The operand of a tap (tz, ty, tx) is the same layout
+// started at plane z + tz, row (1 + ty), column (1 + tx): a descriptor with a
+// shifted start address.
+//
+// Roles: warp 8 (one thread) issues the TMA plane loads (up to kLook planes
+// ahead) and the MMAs into one of two accumulator buffers (2 x 256 columns);
+// warpgroup 0 finishes even planes, warpgroup 1 odd planes: tcgen05.ld of the
+// 8 parity accumulators of its row, LeakyReLU(acc + b3) rounded to bfloat16
+// (as the training decoder rounds g1), D2 on the CUDA cores and the 4 x 4 x 4
+// output block of the latent voxel stored as float4 rows, scaled by the
+// snapshot's rms. mbarriers: plane full (TMA bytes), plane free (commit of
+// the last MMAs that read it), accumulator full (commit), accumulator free
+// (128 epilogue arrivals). Every wait is bounded and shares an abort flag.
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "ae_internal.h"
+#include "tc_gemm.cuh"
+#include "tma_encode.h"
+
+namespace rtm {
+namespace ae {
+namespace {
+
+constexpr int TX = 8, TY = 16;                 // latent column (128 MMA rows)
+constexpr int HX = TX + 2, HY = TY + 2;        // with the halo
+constexpr int kHalfBytes = 2944;               // one 8-channel half plane (2880 B, 128-aligned)
+constexpr int kPlaneBytes = 2 * kHalfBytes;
+constexpr int kTmaBytes = 2 * HX * HY * 16;    // bytes one plane load delivers
+constexpr int kSlots = 9;                      // plane ring
+constexpr int kLook = kSlots - 4;              // planes loaded beyond the newest one needed
+constexpr int kW3Bytes = 64 * 1024;            // 64 B operands (parity, tap): 32 x 16, 1 KB each
+constexpr int kSmem = 128 + kW3Bytes + kSlots * kPlaneBytes + 288 * 4;  // > half an SM: 1 CTA
+constexpr int kTmemCols = 512;
+constexpr int kThreads = 288;
+constexpr long long kLimit = 1LL << 24;
+
+struct Sched {
+    int ncx, ncy, nzc, zc, nitems;
+};
+
+__device__ __forceinline__ void item_coords(const Sched& S, int lnz, int item, int& cx, int& cy,
+                                            int& z0, int& nz) {
+    cx = item % S.ncx;
+    cy = (item / S.ncx) % S.ncy;
+    const int kz = item / (S.ncx * S.ncy);
+    z0 = kz * S.zc;
+    nz = min(S.zc, lnz - z0);
+}
+
+// taps of a transposed conv (kernel 4, stride 2, padding 1) along one axis
+// for output parity q: tap tau reads input i + t with kernel index k
+__device__ __forceinline__ void taps(int q, int tau, int& t, int& k) {
+    if (q == 0) {
+        t = tau ? -1 : 0;
+        k = tau ? 3 : 1;
+    } else {
+        t = tau ? 0 : 1;
+        k = tau ? 2 : 0;
+    }
+}
+
+__device__ __forceinline__ float lrelu(float a) { return a > 0.f ? a : kSlope * a; }
+__device__ __forceinline__ float rbf(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
+
+__device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(b)) : "memory");
+}
+// bounded wait; gives up early once another thread has raised the abort flag
+__device__ __forceinline__ bool wait_bar(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+    const uint32_t a = tc::smem_u32(b);
+    for (long long i = 0; i < kLimit; i++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (abort_flag && *abort_flag) return false;
+    }
+    if (abort_flag) *abort_flag = 1;
+    return false;
+}
+__device__ __forceinline__ void tma_plane(uint8_t* dst, const CUtensorMap* map, int kc, int x, int y,
+                                          int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(tc::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(kc), "r"(x), "r"(y), "r"(z),
+        "r"(tc::smem_u32(bar))
+        : "memory");
+}
+// 16 columns of this warp's lanes, without waiting
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, float* out) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; i++) out[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// byte offset of (row o, k) in a 32 x 16 K-major operand (LBO 128, SBO 256)
+__device__ __forceinline__ int b_off(int o, int k) {
+    return (o >> 3) * 256 + (k >> 3) * 128 + (o & 7) * 16 + (k & 7) * 2;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_decode_march(const __grid_constant__ D12Args A, const __grid_constant__ CUtensorMap map,
+                   const Sched S, int* status) {
+    extern __shared__ uint8_t dsm_raw[];
+    __shared__ __align__(8) uint64_t full[kSlots], freed[kSlots], acc_full[2], acc_free[2], fin;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+
+    uint8_t* base = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(dsm_raw) + 127) & ~static_cast<uintptr_t>(127));
+    uint8_t* w3 = base;
+    uint8_t* ring = base + kW3Bytes;
+    float* w4 = reinterpret_cast<float*>(ring + kSlots * kPlaneBytes);  // [8][32], then b3[32]
+
+    const D1Args& d = A.d1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    volatile int* abrt = &abort_flag;
+
+    if (tid == 0) {
+        for (int s = 0; s < kSlots; s++) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&freed[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            tc::mbar_init(&acc_full[b], 1);
+            tc::mbar_init(&acc_free[b], 128);
+        }
+        tc::mbar_init(&fin, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, kTmemCols);
+    // B operands: (parity q, tap tau) -> W3[o][kz][ky][kx][i] as a 32 x 16 K-major tile
+    for (int idx = tid; idx < 64 * 32 * 2; idx += kThreads) {
+        const int j = idx & 1, o = (idx >> 1) & 31, t = idx >> 6, q = t >> 3, tau = t & 7;
+        int tz, kz, ty, ky, tx, kx;
+        taps(q >> 2, tau >> 2, tz, kz);
+        taps((q >> 1) & 1, (tau >> 1) & 1, ty, ky);
+        taps(q & 1, tau & 1, tx, kx);
+        const int ktap = (kz * 4 + ky) * 4 + kx;
+        float w[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) w[e] = d.P[kOW3 + o * 1024 + ktap * 16 + 8 * j + e];
+        *reinterpret_cast<uint4*>(w3 + t * 1024 + b_off(o, 8 * j)) = tc::pack8(w);
+    }
+    for (int i = tid; i < 256; i += kThreads) w4[i] = rbf(d.P[kOW4 + i]);
+    if (tid < 32) w4[256 + tid] = d.P[kOB3 + tid];
+    tc::fence_proxy_async();
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const int lnx = d.l.nx, lny = d.l.ny, lnz = d.l.nz;
+
+    if (warp == 8) {
+        if (lane == 0) {
+            // ---------------- producer: plane loads and MMAs ----------------
+            constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
+            const uint32_t ring_a = tc::smem_u32(ring);
+            const uint64_t dB0 = tc::sdesc(tc::smem_u32(w3), 128, 256);
+            // load cursor: k-th item of this CTA, plane j of that item, global sequence
+            int l_k = 0, l_j = 0, l_seq = 0, waited = 0;
+            int out = 0, base_seq = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < S.nitems && ok; item += gridDim.x) {
+                int cx, cy, z0, nz;
+                item_coords(S, lnz, item, cx, cy, z0, nz);
+                for (int zi = 0; zi < nz && ok; zi++) {
+                    const int target = base_seq + zi + 2 + kLook;
+                    while (ok && l_seq <= target) {
+                        const int litem = blockIdx.x + l_k * gridDim.x;
+                        if (litem >= S.nitems) break;
+                        int lcx, lcy, lz0, lnzi;
+                        item_coords(S, lnz, litem, lcx, lcy, lz0, lnzi);
+                        const int slot = l_seq % kSlots;
+                        if (l_seq >= kSlots)
+                            ok = wait_bar(&freed[slot], (uint32_t)((l_seq / kSlots - 1) & 1), abrt);
+                        if (!ok) break;
+                        bar_expect(&full[slot], kTmaBytes);
+                        uint8_t* dst = ring + slot * kPlaneBytes;
+                        for (int kc = 0; kc < 2; kc++)
+                            tma_plane(dst + kc * kHalfBytes, &map, kc, lcx * TX - 1, lcy * TY - 1,
+                                      lz0 - 1 + l_j, &full[slot]);
+                        l_seq++;
+                        if (++l_j == lnzi + 2) {
+                            l_j = 0;
+                            l_k++;
+                        }
+                    }
+                    for (int s = base_seq + zi; s <= base_seq + zi + 2 && ok; s++) {
+                        ok = wait_bar(&full[s % kSlots], (uint32_t)((s / kSlots) & 1), abrt);
+                        if (ok && s >= waited) waited = s + 1;
+                    }
+                    const int b = out & 1, u = out >> 1;
+                    if (ok && u >= 1) ok = wait_bar(&acc_free[b], (uint32_t)((u - 1) & 1), abrt);
+                    if (!ok) break;
+                    tc::tc_fence_after();
+                    // descriptors: the start-address field is address >> 4 and no
+                    // operand crosses 256 KB, so offsets add to the field directly
+                    uint64_t dA[3];
+#pragma unroll
+                    for (int t = 0; t < 3; t++)
+                        dA[t] = tc::sdesc(ring_a + ((base_seq + zi + t) % kSlots) * kPlaneBytes,
+                                          kHalfBytes, HX * 16);
+                    // opaque per plane, so that the 64 B descriptors are not hoisted
+                    // out of the loop into registers
+                    uint64_t dB;
+                    asm volatile("mov.b64 %0, %1;" : "=l"(dB) : "l"(dB0));
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+#pragma unroll
+                        for (int tau = 0; tau < 8; tau++) {
+                            int tz, kz, ty, ky, tx, kx;
+                            taps(q >> 2, tau >> 2, tz, kz);
+                            taps((q >> 1) & 1, (tau >> 1) & 1, ty, ky);
+                            taps(q & 1, tau & 1, tx, kx);
+                            tc::mma_bf16(tmem + b * 256 + q * 32,
+                                         dA[1 + tz] + (uint64_t)((1 + ty) * HX + (1 + tx)),
+                                         dB + (uint64_t)((q * 8 + tau) * 64), idesc,
+                                         tau > 0 ? 1u : 0u);
+                        }
+                    }
+                    tc::mma_commit(&acc_full[b]);
+                    // plane z - 1 is read by no later output of this item
+                    tc::mma_commit(&freed[(base_seq + zi) % kSlots]);
+                    if (zi == nz - 1) {
+                        tc::mma_commit(&freed[(base_seq + zi + 1) % kSlots]);
+                        tc::mma_commit(&freed[(base_seq + zi + 2) % kSlots]);
+                    }
+                    out++;
+                }
+                base_seq += nz + 2;
+            }
+            if (!ok) {
+                *abrt = 1;
+                // loads still in flight must land before the CTA leaves
+                for (int s = waited; s < l_seq; s++)
+                    wait_bar(&full[s % kSlots], (uint32_t)((s / kSlots) & 1), nullptr);
+            }
+            tc::mma_commit(&fin);
+            if (!wait_bar(&fin, 0, nullptr)) *abrt = 1;
+        }
+    } else {
+        // ---------------- epilogue warpgroups ----------------
+        const int g = warp >> 2, row = tid & 127, ly = row >> 3, lx = row & 7;
+        const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        const float b4 = d.P[kOB4];
+        const float sc = A.sigma ? *A.sigma : 1.0f;
+        const bool vec = ((reinterpret_cast<uintptr_t>(A.out.p) & 15) == 0) &&
+                         (A.out.sy % 4 == 0) && (A.out.sz % 4 == 0);
+        const float4* w4v = reinterpret_cast<const float4*>(w4);
+        int out = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < S.nitems && ok; item += gridDim.x) {
+            int cx, cy, z0, nz;
+            item_coords(S, lnz, item, cx, cy, z0, nz);
+            const int X = cx * TX + lx, Y = cy * TY + ly;
+            const bool valid = X < lnx && Y < lny;
+            for (int zi = 0; zi < nz; zi++, out++) {
+                if ((out & 1) != g) continue;
+                const int u = out >> 1;
+                ok = wait_bar(&acc_full[g], (uint32_t)(u & 1), abrt);
+                if (!ok) break;
+                tc::tc_fence_after();
+                const int Z = z0 + zi;
+                const uint32_t tb = lane_base + g * 256;
+#pragma unroll 1
+                for (int qzy = 0; qzy < 4; qzy++) {
+                    const int qz = qzy >> 1, qy = qzy & 1;
+                    float a0[32], a1[32];
+                    tmem_ld16_nw(tb + (qzy * 2) * 32, a0);
+                    tmem_ld16_nw(tb + (qzy * 2) * 32 + 16, a0 + 16);
+                    tmem_ld16_nw(tb + (qzy * 2 + 1) * 32, a1);
+                    tmem_ld16_nw(tb + (qzy * 2 + 1) * 32 + 16, a1 + 16);
+                    tmem_wait_ld();
+                    if (!valid) continue;
+#pragma unroll
+                    for (int c4 = 0; c4 < 8; c4++) {
+                        const float4 bb = w4v[64 + c4];
+                        const float b_[4] = {bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+                        for (int i = 0; i < 4; i++) {
+                            a0[4 * c4 + i] = rbf(lrelu(a0[4 * c4 + i] + b_[i]));
+                            a1[4 * c4 + i] = rbf(lrelu(a1[4 * c4 + i] + b_[i]));
+                        }
+                    }
+#pragma unroll 1
+                    for (int ezy = 0; ezy < 4; ezy++) {
+                        const int e0 = ezy * 2;  // ex = 0; e0 + 1: ex = 1
+                        float y00 = 0.f, y01 = 0.f, y10 = 0.f, y11 = 0.f;
+#pragma unroll
+                        for (int c4 = 0; c4 < 8; c4++) {
+                            const float4 wa = w4v[e0 * 8 + c4], wb = w4v[(e0 + 1) * 8 + c4];
+                            const float wa_[4] = {wa.x, wa.y, wa.z, wa.w};
+                            const float wb_[4] = {wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                            for (int i = 0; i < 4; i++) {
+                                const int c = 4 * c4 + i;
+                                y00 = fmaf(wa_[i], a0[c], y00);
+                                y01 = fmaf(wb_[i], a0[c], y01);
+                                y10 = fmaf(wa_[i], a1[c], y10);
+                                y11 = fmaf(wb_[i], a1[c], y11);
+                            }
+                        }
+                        const int ez = ezy >> 1, ey = ezy & 1;
+                        float* o = A.out.p + (long long)(4 * Z + 2 * qz + ez) * A.out.sz +
+                                   (long long)(4 * Y + 2 * qy + ey) * A.out.sy + 4 * X;
+                        const float4 v = make_float4(sc * (y00 + b4), sc * (y01 + b4),
+                                                     sc * (y10 + b4), sc * (y11 + b4));
+                        if (vec) {
+                            *reinterpret_cast<float4*>(o) = v;
+                        } else {
+                            o[0] = v.x;
+                            o[1] = v.y;
+                            o[2] = v.z;
+                            o[3] = v.w;
+                        }
+                    }
+                }
+                tc::tc_fence_before();
+                bar_arrive(&acc_free[g]);
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && *abrt && status) atomicCAS(status, 0, tc::kErrTimeout);
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// decoder choice: 0 auto (z-marching kernel when TMA is available), 1 the
+// GEMM-engine decoder, 2 the z-marching kernel
+int g_decoder = 0;
+
+}  // namespace
+}  // namespace ae
+
+void ae_set_decoder(int which) { ae::g_decoder = which; }
+
+// Returns cudaErrorNotSupported when the z-marching kernel cannot run (no
+// tensor-map encoder, misaligned latent, or not selected): the caller then
+// uses the GEMM-engine decoder.
+cudaError_t ae_decode_march(const ae::D12Args& a, int* status, cudaStream_t s) {
+    using namespace ae;
+    if (g_decoder == 1) return cudaErrorNotSupported;
+    EncodeTiledFn enc = tma_encoder();
+    if (!enc || (reinterpret_cast<uintptr_t>(a.d1.lat) & 15)) return cudaErrorNotSupported;
+    static int nsm = 0;
+    if (nsm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_decode_march,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (nsm < 1) nsm = 1;
+    }
+    const Dims3 l = a.d1.l;
+    CUtensorMap map;
+    memset(&map, 0, sizeof map);
+    const cuuint64_t dims[5] = {8, 2, (cuuint64_t)l.nx, (cuuint64_t)l.ny, (cuuint64_t)l.nz};
+    const cuuint64_t strides[4] = {16, 32, 32ull * l.nx, 32ull * l.nx * l.ny};
+    const cuuint32_t box[5] = {8, 1, HX, HY, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(a.d1.lat), dims, strides,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorNotSupported;
+    // z chunk: smallest per-CTA makespan, counting each chunk's two halo
+    // planes as one plane of work
+    Sched S;
+    S.ncx = (l.nx + TX - 1) / TX;
+    S.ncy = (l.ny + TY - 1) / TY;
+    const long long ncol = (long long)S.ncx * S.ncy;
+    long long best = -1;
+    S.zc = l.nz;
+    for (int zc = std::min(4, l.nz); zc <= l.nz; zc++) {
+        const long long items = ncol * ((l.nz + zc - 1) / zc);
+        const long long span = (items + nsm - 1) / nsm * (zc + 1);
+        if (best < 0 || span < best) {
+            best = span;
+            S.zc = zc;
+        }
+    }
+    S.nzc = (l.nz + S.zc - 1) / S.zc;
+    S.nitems = (int)(ncol * S.nzc);
+    const int grid = std::min(nsm, S.nitems);
+    k_decode_march<<<grid, kThreads, kSmem, s>>>(a, map, S, status);
+    return cudaGetLastError();
+}
+
+}  // namespace rtm

@@ -68,6 +68,12 @@ cudaError_t ae_encode(const float* P, const ae::Vol& in, ae::bf16* h1, ae::bf16*
 // decoder layers run fused (inference), otherwise g1 keeps the D1 output
 cudaError_t ae_decode(const float* P, const ae::bf16* lat, const float* sigma, const ae::Vol& out,
                       ae::bf16* g1, int* status, cudaStream_t s);
+// the fused inference decoder as one z-marching persistent kernel (TMA plane
+// loads read in place by the tensor cores); cudaErrorNotSupported when it
+// cannot run or is not selected
+cudaError_t ae_decode_march(const ae::D12Args& a, int* status, cudaStream_t s);
+// 0 automatic, 1 GEMM-engine decoder, 2 z-marching decoder
+void ae_set_decoder(int which);
 cudaError_t ae_sample_grad(const float* P, const ae::Vol& in, float scale,
                            const ae::AeTrainBufs& b, ae::AeScalars* sc, double* loss, float* grad,
                            int* status, cudaStream_t s);

@@ -25,6 +25,7 @@
 
 #include "rtm_internal.h"
 #include "stencil_common.cuh"
+#include "tma_encode.h"
 
 namespace rtm {
 
@@ -83,8 +84,17 @@ __device__ __forceinline__ void tma3(float* dst, const CUtensorMap* map, int x, 
         : "memory");
 }
 
+// resident blocks per SM: with two pointwise operand rings (the forward
+// modes) a radius-4 block needs 73 KB of shared memory, so three fit when the
+// registers are capped at 80 per thread; the backward modes (four rings,
+// 98 KB) fit two
 template <int R, int MODE>
-__global__ void __launch_bounds__(256, R == 4 ? 2 : 1)
+constexpr int tma_min_blocks() {
+    return R != 4 ? 1 : ((MODE == MODE_BWD_IMAGE || MODE == MODE_BWD_GRAD) ? 2 : 3);
+}
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
     k_stencil_tma(const __grid_constant__ StepArgs A, const __grid_constant__ TmaMaps M, int* status) {
     using T = Tile<R>;
     constexpr int NA = (MODE == MODE_BWD_IMAGE || MODE == MODE_BWD_GRAD) ? 4 : 2;
@@ -251,27 +261,8 @@ __global__ void __launch_bounds__(256, R == 4 ? 2 : 1)
 }
 
 // ---- host side: tensor maps ---------------------------------------------------
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-    static std::once_flag once;
-    static EncodeTiledFn fn = nullptr;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                             &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    });
-    return fn;
-}
-
 cudaError_t make_map(CUtensorMap* m, const float* base, int nx, int ny, int nz, int bx, int by) {
-    EncodeTiledFn f = encode_fn();
+    EncodeTiledFn f = tma_encoder();
     if (!f) return cudaErrorNotSupported;
     if (((uintptr_t)base % 16) || (nx % 4)) return cudaErrorInvalidValue;
     const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
@@ -293,6 +284,10 @@ cudaError_t launch_tma_t(const StepArgs& a, int* status, cudaStream_t s) {
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_stencil_tma<R, MODE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_stencil_tma<R, MODE>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -331,7 +326,21 @@ cudaError_t launch_tma_r(int mode, const StepArgs& a, int* status, cudaStream_t 
 
 }  // namespace
 
-bool tma_available() { return encode_fn() != nullptr; }
+EncodeTiledFn tma_encoder() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+bool tma_available() { return tma_encoder() != nullptr; }
 
 cudaError_t launch_stencil_tma(int radius, int mode, const StepArgs& a, int* status,
                                cudaStream_t s) {

@@ -106,6 +106,41 @@ def test_strided_snapshot_views_encode_identically():
     assert bool((out[:, :, :5] == 7.0).all()) and bool((out[:, :, 25:] == 7.0).all())
 
 
+@pytest.mark.parametrize("shape", [(4, 4, 4), (32, 32, 32), (20, 28, 36), (160, 96, 72)])
+def test_marching_decoder_equals_gemm_decoder(shape):
+    """The z-marching decoder (TMA plane loads read in place by the tensor
+    cores, several z chunks and ragged x / y columns at the largest shape)
+    and the GEMM-engine decoder form the same sums in the same order: equal
+    outputs, into dense arrays and into strided views whose rows are not
+    16-byte aligned."""
+    import torch
+
+    from paper_1603_03971_gb300 import codec
+
+    nz, ny, nx = shape
+    P = _cuda(_params(5))
+    lat = _cuda(0.5 * rtm_inputs.standard_normal((nz // 4, ny // 4, nx // 4, 16), 61),
+                torch.bfloat16)
+    sc = torch.tensor([1.7], device="cuda")
+    ws = codec.alloc_workspace(shape)
+    try:
+        codec.set_decoder("gemm")
+        ref = codec.decode(P, lat, sc, ws)
+        codec.set_decoder("march")
+        out = codec.decode(P, lat, sc, ws)
+        big = torch.full((nz, ny, nx + 5), float("nan"), device="cuda")
+        codec.decode(P, lat, sc, ws, out=big[:, :, 1:1 + nx])
+        torch.cuda.synchronize()
+    finally:
+        codec.set_decoder("auto")
+    import paper_1603_03971_gb300 as rtm
+
+    rtm.check(ws)
+    assert torch.equal(out, ref)
+    assert torch.equal(big[:, :, 1:1 + nx], ref)
+    assert bool(big[:, :, 0].isnan().all()) and bool(big[:, :, 1 + nx:].isnan().all())
+
+
 @pytest.mark.parametrize("shape", [(16, 16, 16), (20, 12, 24)])
 def test_training_gradient_matches_oracle(shape):
     import torch
