@@ -34,8 +34,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gpoint-updates/s vs HBM roofline; RTM shot time learned vs checkpoint @≤1e-2"
 UNIT = "Gpoint-updates/s"
-PROFILE = os.path.join(ROOT, "profiles", "stencil_bwd_image_r4_smooth512.md")
-STENCIL_SRC = os.path.join(ROOT, "paper_1603_03971_gb300", "csrc", "stencil.cu")
+PROFILE = os.path.join(ROOT, "profiles", "stencil_tma_bwd_image_r4_smooth512.md")
+STENCIL_SRC = os.path.join(ROOT, "paper_1603_03971_gb300", "csrc", "stencil_tma.cu")
 
 
 def parse():
@@ -454,7 +454,8 @@ def run_ours(args):
     achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else None
     shares = {k: v["ms"] for k, v in st["stencil"].items() if v["launches"]}
     roofline = {
-        "kernel": "k_stencil<4, MODE_BWD_IMAGE> (backward step + fused zero-lag imaging)",
+        "kernel": ("k_stencil_tma<4, MODE_BWD_IMAGE>" if args.variant != 1 else
+                   "k_stencil<4, MODE_BWD_IMAGE>") + " (backward step + fused zero-lag imaging)",
         "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
         "frac": (achieved / hbm) if achieved else None, "peak_kind": peak_kind,
         "traffic": profiled_traffic(), "algorithmic_bytes_per_launch": per_launch_bytes,

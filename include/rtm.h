@@ -263,6 +263,16 @@ rtm_status rtm_ae_train_step(float *d_params, float *d_adam_m, float *d_adam_v, 
  * Both give the same values. Process-wide; returns RTM_ERR_INVALID for other
  * values. */
 rtm_status rtm_ae_set_decoder(int32_t which);
+/* Inference encoder used by rtm_ae_encode and the learned-storage forward
+ * pass: 0 automatic (the z-marching kernel: snapshot planes loaded by TMA, E1
+ * on the CUDA cores into shared memory, E2 on the tensor cores reading it in
+ * place, one persistent CTA per SM; the GEMM-engine encoder when the driver
+ * has no tensor-map encoder or the snapshot rows are not 16-byte aligned),
+ * 1 the GEMM-engine encoder, 2 the z-marching kernel where it can run. The two
+ * differ only where E1's float32 sums, formed in another order, round to
+ * neighbouring bfloat16 values. Process-wide; returns RTM_ERR_INVALID for
+ * other values. */
+rtm_status rtm_ae_set_encoder(int32_t which);
 /* The tensor-core engine under the codec, exposed for checking: C[M][N] =
  * A[M][K] * B[N][K]^T, bfloat16 in, float32 out, K a multiple of 32, N 16 or
  * 32. A bounded wait that runs out writes RTM_ERR_TIMEOUT to *d_status. */

@@ -97,6 +97,7 @@ SIGNATURES = {
                                          _i32, _i32, _vp, _vp, _vp, _sz, _vp]),
     "rtm_ae_gemm_bf16": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     "rtm_ae_set_decoder": (ctypes.c_int, [_i32]),
+    "rtm_ae_set_encoder": (ctypes.c_int, [_i32]),
     "rtm_set_timing": (ctypes.c_int, [_i32]),
     "rtm_stats_get": (ctypes.c_int, [ctypes.POINTER(RtmStats)]),
     "rtm_stats_reset": (ctypes.c_int, []),

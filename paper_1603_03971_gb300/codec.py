@@ -116,6 +116,13 @@ def set_decoder(which: str = "auto") -> None:
     call("rtm_ae_set_decoder", code)
 
 
+def set_encoder(which: str = "auto") -> None:
+    """Inference encoder: "auto", "gemm" (GEMM-engine encoder) or "march"
+    (z-marching kernel: E1 into shared memory, E2 on the tensor cores)."""
+    code = {"auto": 0, "gemm": 1, "march": 2}[which]
+    call("rtm_ae_set_encoder", code)
+
+
 def _time_codec(n: int, reps: int = 10, seed: int = 0):
     """Encode and decode of a random n^3 snapshot; returns (encode ms, decode ms)."""
     import numpy as np

@@ -898,15 +898,19 @@ cudaError_t ae_rms(const Vol& in, AeScalars* sc, cudaStream_t s) {
 }
 
 cudaError_t ae_encode(const float* P, const Vol& in, bf16* h1, bf16* lat, AeScalars* sc,
-                      float* sigma_out, int* status, cudaStream_t s) {
+                      float* sigma_out, int* status, cudaStream_t s, bool keep_h1) {
     cudaError_t e = ae_rms(in, sc, s);
     if (e != cudaSuccess) return e;
     const Dims3 h{in.nx / 2, in.ny / 2, in.nz / 2}, l{in.nx / 4, in.ny / 4, in.nz / 4};
-    E1Args a1{in, &sc->inv_sigma, P, h1, h};
-    e = run<OpE1>(a1, dim3(tiles((long long)h.nx * h.ny * h.nz)), status, s);
-    if (e != cudaSuccess) return e;
-    E2Args a2{h1, h, P, lat, l};
-    e = run_async<OpE2>(a2, dim3(tiles((long long)l.nx * l.ny * l.nz)), status, s);
+    e = keep_h1 ? cudaErrorNotSupported : ae_encode_march(P, in, &sc->inv_sigma, lat, status, s);
+    if (e == cudaErrorNotSupported) {
+        cudaGetLastError();
+        E1Args a1{in, &sc->inv_sigma, P, h1, h};
+        e = run<OpE1>(a1, dim3(tiles((long long)h.nx * h.ny * h.nz)), status, s);
+        if (e != cudaSuccess) return e;
+        E2Args a2{h1, h, P, lat, l};
+        e = run_async<OpE2>(a2, dim3(tiles((long long)l.nx * l.ny * l.nz)), status, s);
+    }
     if (e != cudaSuccess) return e;
     if (sigma_out) e = cudaMemcpyAsync(sigma_out, &sc->sigma, sizeof(float),
                                        cudaMemcpyDeviceToDevice, s);
@@ -937,7 +941,7 @@ cudaError_t ae_sample_grad(const float* P, const Vol& in, float scale, const AeT
     const Dims3 h{in.nx / 2, in.ny / 2, in.nz / 2}, l{in.nx / 4, in.ny / 4, in.nz / 4};
     const long long nh = (long long)h.nx * h.ny * h.nz, nl = (long long)l.nx * l.ny * l.nz;
     const long long n = (long long)in.nx * in.ny * in.nz;
-    cudaError_t e = ae_encode(P, in, b.h1, b.lat, sc, nullptr, status, s);
+    cudaError_t e = ae_encode(P, in, b.h1, b.lat, sc, nullptr, status, s, true);
     if (e != cudaSuccess) return e;
     const Vol yv{b.y, (long long)in.nx, (long long)in.nx * in.ny, in.nx, in.ny, in.nz};
     e = ae_decode(P, b.lat, nullptr, yv, b.g1, status, s);

@@ -177,6 +177,13 @@ rtm_status rtm_ae_gemm_bf16(const uint16_t* d_A, const uint16_t* d_B, float* d_C
     return RTM_OK;
 }
 
+rtm_status rtm_ae_set_encoder(int32_t which) {
+    if (which < 0 || which > 2)
+        return (rtm_status)set_error(RTM_ERR_INVALID, "encoder: 0 automatic, 1 GEMM engine, 2 z-marching");
+    ae_set_encoder(which);
+    return RTM_OK;
+}
+
 rtm_status rtm_ae_set_decoder(int32_t which) {
     if (which < 0 || which > 2)
         return (rtm_status)set_error(RTM_ERR_INVALID, "decoder: 0 automatic, 1 GEMM engine, 2 z-marching");

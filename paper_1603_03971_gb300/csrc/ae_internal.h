@@ -61,9 +61,13 @@ struct AeTrainBufs {
 
 cudaError_t ae_gemm_test(const ae::GemmArgs& a, int N, int* status, cudaStream_t s);
 cudaError_t ae_rms(const ae::Vol& in, ae::AeScalars* sc, cudaStream_t s);
-// snapshot -> latent (h1 is scratch); the snapshot's rms goes to sigma_out if given
+// snapshot -> latent; the snapshot's rms goes to sigma_out if given. With
+// keep_h1 the GEMM-engine layers run and leave E1's output in h1 (training
+// reads it); otherwise the z-marching kernel runs where it can and h1 is
+// untouched scratch.
 cudaError_t ae_encode(const float* P, const ae::Vol& in, ae::bf16* h1, ae::bf16* lat,
-                      ae::AeScalars* sc, float* sigma_out, int* status, cudaStream_t s);
+                      ae::AeScalars* sc, float* sigma_out, int* status, cudaStream_t s,
+                      bool keep_h1 = false);
 // latent -> snapshot scaled by *sigma (1 if NULL); with g1 NULL the two
 // decoder layers run fused (inference), otherwise g1 keeps the D1 output
 cudaError_t ae_decode(const float* P, const ae::bf16* lat, const float* sigma, const ae::Vol& out,
@@ -74,6 +78,12 @@ cudaError_t ae_decode(const float* P, const ae::bf16* lat, const float* sigma, c
 cudaError_t ae_decode_march(const ae::D12Args& a, int* status, cudaStream_t s);
 // 0 automatic, 1 GEMM-engine decoder, 2 z-marching decoder
 void ae_set_decoder(int which);
+// E1 + E2 as one z-marching persistent kernel (h1 kept in shared memory);
+// cudaErrorNotSupported when it cannot run or is not selected
+cudaError_t ae_encode_march(const float* P, const ae::Vol& in, const float* inv_sigma,
+                            ae::bf16* lat, int* status, cudaStream_t s);
+// 0 automatic, 1 GEMM-engine encoder, 2 z-marching encoder
+void ae_set_encoder(int which);
 cudaError_t ae_sample_grad(const float* P, const ae::Vol& in, float scale,
                            const ae::AeTrainBufs& b, ae::AeScalars* sc, double* loss, float* grad,
                            int* status, cudaStream_t s);

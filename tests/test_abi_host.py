@@ -104,6 +104,8 @@ def test_calls_reject_bad_arguments_without_a_device():
     assert L.rtm_ae_set_decoder(3) == 1
     assert L.rtm_ae_set_decoder(-1) == 1
     assert L.rtm_ae_set_decoder(0) == 0
+    assert L.rtm_ae_set_encoder(3) == 1
+    assert L.rtm_ae_set_encoder(0) == 0
 
 
 def test_workspace_sizes_follow_the_storage_policy():
