@@ -56,11 +56,14 @@ def parse():
                     help="oracle time steps per bench step of the reference arm")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-compression leg (384^3, 3000 steps)")
-    ap.add_argument("--learned-train-steps", type=int, default=2000)
-    ap.add_argument("--learned-models", type=int, default=24)
+    ap.add_argument("--learned-train-steps", type=int, default=4000)
+    ap.add_argument("--learned-models", type=int, default=64)
     ap.add_argument("--batch", action="store_true",
                     help="also run the batched-shots leg (32 apertures, radius 8)")
     ap.add_argument("--batch-nt", type=int, default=1500)
+    ap.add_argument("--imaging", action="store_true",
+                    help="also time the imaging-condition variants (source illumination, "
+                         "normalised and Laplacian-filtered image) on the main workload")
     ap.add_argument("--variant", type=int, default=0,
                     help="stencil plane-load variant: 0 automatic, 1 vector loads, 2 TMA")
     return ap.parse_args()
@@ -288,9 +291,17 @@ def learned_leg(args, dev):
     rec = torch.from_numpy(w.receivers()).to(dev)
     pc = rtm.params_for(w, storage="ckpt", ckpt_every=50)
     ws = rtm.alloc_workspace(pc, dev)
-    c = rtm.model_prep(pc, v, ws)
+    # observed data: the scattered field of thin beds (data of the model with
+    # the beds minus the direct field of the smooth migration model)
+    c_true = rtm.model_prep(pc, rtm_inputs.thin_bed_reflectors(v).contiguous(), ws)
     dobs = torch.empty((w.nt, pc.nrec), dtype=torch.float32, device=dev)
-    rtm.forward(pc, c, rec, ws, data=dobs)
+    rtm.forward(pc, c_true, rec, ws, data=dobs)
+    del c_true
+    c = rtm.model_prep(pc, v, ws)
+    d_direct = torch.empty_like(dobs)
+    rtm.forward(pc, c, rec, ws, data=d_direct)
+    dobs -= d_direct
+    del d_direct
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     img_c = torch.zeros((w.nz, w.ny, w.nx), dtype=torch.float32, device=dev)
@@ -315,22 +326,68 @@ def learned_leg(args, dev):
     torch.cuda.synchronize()
     t_learned = e0.elapsed_time(e1) / 1e3
     rtm.check(wl)
+    from paper_1603_03971_gb300 import codec
+
+    enc_ms, dec_ms = codec._time_codec(w.nx, reps=10)
     err = float((img_l - img_c).norm() / img_c.norm())
     err_deep = float((img_l[16:] - img_c[16:]).norm() / img_c[16:].norm())
     NZ, NY, NX = w.padded_shape
     return {
         "workload": "learned_384: 384^3 model (448^3 padded), r=4, 3000 steps, smooth random "
-                    "velocity, imaging every 4 steps (750 snapshots)",
+                    "velocity, imaging every 4 steps (750 snapshots); observed data: scattered "
+                    "field of three thin beds (+-8 %) at depths 96/192/288",
         "shot_s_checkpoint": t_ckpt, "checkpoint_every": 50,
         "shot_s_learned": t_learned, "speedup_vs_checkpoint": t_ckpt / t_learned,
         "image_rel_l2_vs_checkpoint": err, "target_rel_l2": 1e-2,
         "image_rel_l2_below_z16": err_deep,
+        "codec_ms_per_snapshot": {"encode": enc_ms, "decode": dec_ms},
         "compression": "8x (float32 snapshot -> 16 bfloat16 channels per 4^3 voxels)",
         "train": {"models": args.learned_models, "snapshots": n_snap,
                   "steps": args.learned_train_steps, "batch": 4, "seconds": train_s,
                   "final_loss": losses[-1][1]},
         "updates_per_shot_learned": 2 * w.nt * NX * NY * NZ,
     }
+
+
+def imaging_leg(p, c, rec, dobs, ws, dev):
+    """The receiver pass with and without the source-illumination
+    accumulation (same checkpoints, recomputed each time), and the image
+    filters, on the main workload; CUDA events on the launching stream."""
+    import torch
+
+    import paper_1603_03971_gb300 as rtm
+
+    img = torch.zeros((p.nz, p.ny, p.nx), dtype=torch.float32, device=dev)
+    illum = torch.zeros_like(img)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        rtm.forward(p, c, rec, ws)
+        torch.cuda.synchronize()
+        ev[0].record()
+        fn()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / 1e3
+
+    t_plain = timed(lambda: rtm.backward_image(p, c, rec, dobs, ws, img))
+    t_illum = timed(lambda: rtm.backward_image_illum(p, c, rec, dobs, ws, img, illum))
+    rtm.check(ws)
+    torch.cuda.synchronize()
+    ev[0].record()
+    rtm.image_filter(p, img, ws, illum=illum, eps_rel=1e-3)
+    ev[1].record()
+    torch.cuda.synchronize()
+    t_filter = ev[0].elapsed_time(ev[1]) / 1e3
+    nmodel = p.nx * p.ny * p.nz
+    n_img = p.nt // p.image_every
+    illum_bytes = 12.0 * nmodel * n_img  # snapshot read, illumination read + write
+    extra = t_illum - t_plain
+    return {"backward_s": t_plain, "backward_with_illumination_s": t_illum,
+            "illumination_overhead_s": extra,
+            "illumination_pass_gbs": illum_bytes / extra / 1e9 if extra > 0 else None,
+            "illumination_bytes_per_step": 12.0 * nmodel,
+            "filter_s": t_filter}
 
 
 def batch_leg(args, dev):
@@ -487,6 +544,9 @@ def run_ours(args):
 
     if world > 1:
         shots.stack_images(image)  # the multi-shot stack (outside the timed region)
+    imaging_res = None
+    if rank == 0 and args.imaging:
+        imaging_res = imaging_leg(p, c, rec, dobs, ws, dev)
     del vel
     learned = None
     if rank == 0 and not args.no_learned:
@@ -519,6 +579,7 @@ def run_ours(args):
             "config": cfg, "shot_s": t_max / args.steps, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": st["launches"],
             "clocks": clocks, "impl": "ours", "learned": learned, "batch": batch_res,
+            "imaging": imaging_res,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

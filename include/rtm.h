@@ -111,7 +111,9 @@ rtm_status rtm_validate(const rtm_params *p);
 /* Workspace bytes that rtm_forward / rtm_backward_image / rtm_shot / rtm_grad
  * need for p (0 if p is invalid). The same workspace must be passed to the
  * forward call and to the backward call that consumes its snapshots or
- * checkpoints. */
+ * checkpoints. A checkpointed backward call recomputes each segment in place
+ * in its checkpoint slot, so one forward call feeds one backward call;
+ * store-all and learned storage may be imaged more than once. */
 size_t rtm_workspace_size(const rtm_params *p);
 
 /* Model preparation (the padded coefficient grid).
@@ -264,20 +266,46 @@ rtm_status rtm_ae_train_step(float *d_params, float *d_adam_m, float *d_adam_v, 
  * values. */
 rtm_status rtm_ae_set_decoder(int32_t which);
 /* Inference encoder used by rtm_ae_encode and the learned-storage forward
- * pass: 0 automatic (the z-marching kernel: snapshot planes loaded by TMA, E1
- * on the CUDA cores into shared memory, E2 on the tensor cores reading it in
- * place, one persistent CTA per SM; the GEMM-engine encoder when the driver
- * has no tensor-map encoder or the snapshot rows are not 16-byte aligned),
- * 1 the GEMM-engine encoder, 2 the z-marching kernel where it can run. The two
- * differ only where E1's float32 sums, formed in another order, round to
- * neighbouring bfloat16 values. Process-wide; returns RTM_ERR_INVALID for
- * other values. */
+ * pass: 0 automatic (the z-marching kernel: snapshot planes loaded by TMA,
+ * E1 and E2 on the tensor cores with h1 kept in shared memory, one
+ * persistent CTA per SM; the GEMM-engine encoder when the driver has no
+ * tensor-map encoder or the snapshot rows are not 16-byte aligned), 1 the
+ * GEMM-engine encoder, 2 the z-marching kernel where it can run. Both give
+ * the same values. Process-wide; returns RTM_ERR_INVALID for other values. */
 rtm_status rtm_ae_set_encoder(int32_t which);
 /* The tensor-core engine under the codec, exposed for checking: C[M][N] =
  * A[M][K] * B[N][K]^T, bfloat16 in, float32 out, K a multiple of 32, N 16 or
  * 32. A bounded wait that runs out writes RTM_ERR_TIMEOUT to *d_status. */
 rtm_status rtm_ae_gemm_bf16(const uint16_t *d_A, const uint16_t *d_B, float *d_C, int32_t M,
                             int32_t K, int32_t N, int32_t *d_status, rtm_stream stream);
+
+/* ---- imaging-condition variants -------------------------------------------
+ * The paper forms the image by zero-lag cross-correlation of the source and
+ * receiver wavefields (Sec. I) and says nothing about post-processing; these
+ * are the two standard companions of that condition.
+ *
+ * rtm_backward_image_illum: rtm_backward_image (or, with storage =
+ * RTM_STORE_LEARNED and d_ae_params given, rtm_backward_image_learned) that
+ * also accumulates the source illumination d_illum[z][y][x] += sum over the
+ * imaging steps m of u^m(x)^2, from the same snapshots the image uses
+ * (decoded ones in learned storage). d_illum: model grid [nz][ny][nx], float32,
+ * caller-owned, added to.
+ *
+ * rtm_image_filter: on the model grid [nz][ny][nx], d_normalized (if not NULL)
+ * = image / (illum + eps_rel * max(illum)), eps_rel > 0 (the maximum is
+ * reduced on the device into the status block of d_ws, which must be an RTM
+ * workspace of at least 256 bytes); d_laplacian (if not NULL) = -L image with
+ * the 2r-order star of p->radius divided by dx^2 and zero outside the model
+ * grid (suppresses the low-wavenumber backscatter of zero-lag imaging).
+ * Only p->nx, ny, nz, radius and dx are read. Outputs must not alias the
+ * inputs. */
+rtm_status rtm_backward_image_illum(const rtm_params *p, const float *d_c, const int32_t *d_rec,
+                                    const float *d_rdata, const float *d_ae_params, void *d_ws,
+                                    size_t ws_bytes, float *d_image, float *d_illum,
+                                    rtm_stream stream);
+rtm_status rtm_image_filter(const rtm_params *p, const float *d_image, const float *d_illum,
+                            float eps_rel, float *d_normalized, float *d_laplacian, void *d_ws,
+                            size_t ws_bytes, rtm_stream stream);
 
 /* ---- batched shots on uneven apertures (one persistent launch per wave) ----
  * Each shot runs a full RTM (forward modelling with checkpoints every

@@ -174,6 +174,33 @@ def shot_learned(p: RtmParams, c, rec, dobs, ae_params, ws, image, stream=None):
     return image
 
 
+def backward_image_illum(p: RtmParams, c, rec, rdata, ws, image, illum, ae_params=None,
+                         stream=None):
+    """Receiver propagation with the zero-lag image (added to ``image``) and
+    the source illumination ``sum_m (u^m)^2`` over the imaging steps (added to
+    ``illum``, model grid). Learned storage needs ``ae_params``."""
+    w, wb = _ws(ws)
+    call("rtm_backward_image_illum", ctypes.byref(p), _dev(c, name="c"),
+         _dev(rec, torch.int32, "rec"), _dev(rdata, name="rdata"),
+         _dev(ae_params, name="ae_params"), w, wb, _dev(image, name="image"),
+         _dev(illum, name="illum"), _stream(stream))
+    return image, illum
+
+
+def image_filter(p: RtmParams, image, ws, illum=None, eps_rel: float = 1e-3,
+                 normalized=True, laplacian=True, stream=None):
+    """Illumination-normalised image ``I / (illum + eps_rel max illum)`` and/or
+    Laplacian-filtered image ``-L I`` (model grid). Returns (normalised or
+    None, laplacian or None)."""
+    w, wb = _ws(ws)
+    norm = torch.empty_like(image) if normalized else None
+    lap = torch.empty_like(image) if laplacian else None
+    call("rtm_image_filter", ctypes.byref(p), _dev(image, name="image"),
+         _dev(illum, name="illum"), ctypes.c_float(eps_rel), _dev(norm, name="normalized"),
+         _dev(lap, name="laplacian"), w, wb, _stream(stream))
+    return norm, lap
+
+
 def snapshot(p: RtmParams, ws, m: int, out=None, stream=None):
     """Stored imaging snapshot u^m of a store-all workspace (model grid)."""
     if out is None:

@@ -87,6 +87,9 @@ SIGNATURES = {
     "rtm_batch_workspace_size": (_sz, [_P, _i32, _vp, _sz]),
     "rtm_batch_set_wait": (ctypes.c_int, [ctypes.c_double, _i32]),
     "rtm_batch": (ctypes.c_int, [_P, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _sz, _i32, _vp]),
+    "rtm_backward_image_illum": (ctypes.c_int, [_P, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _vp,
+                                                _vp]),
+    "rtm_image_filter": (ctypes.c_int, [_P, _vp, _vp, ctypes.c_float, _vp, _vp, _vp, _sz, _vp]),
     "rtm_ae_param_count": (_sz, []),
     "rtm_ae_workspace_size": (_sz, [_i32, _i32, _i32]),
     "rtm_ae_encode": (ctypes.c_int, [_vp, _vp, _i64, _i64, _i32, _i32, _i32, _vp, _vp, _vp, _sz,

@@ -118,7 +118,8 @@ def set_decoder(which: str = "auto") -> None:
 
 def set_encoder(which: str = "auto") -> None:
     """Inference encoder: "auto", "gemm" (GEMM-engine encoder) or "march"
-    (z-marching kernel: E1 into shared memory, E2 on the tensor cores)."""
+    (z-marching kernel: h1 kept in shared memory, E1 and E2 on the tensor
+    cores). Both give the same values."""
     code = {"auto": 0, "gemm": 1, "march": 2}[which]
     call("rtm_ae_set_encoder", code)
 

@@ -9,18 +9,22 @@
 // computed from two snapshot planes, which TMA copies (40 x 66 floats, zeros
 // outside the volume) into a four-slot ring.
 //
-// E1 runs on the CUDA cores: x0 = bf16(s / rms), h1 = bf16(LeakyReLU(W1 x0 +
-// b1)) with W1 rounded to bf16, the rounding points of the training encoder.
-// Warpgroup 1 computes even h1 planes, warpgroup 2 odd ones (each with two
-// snapshot slots, so that its next plane's copy overlaps its compute), each
-// thread one voxel x 8 channels per unit, into a three-slot h1 ring laid out
-// as E2's A operand in the canonical K-major no-swizzle layout: four
-// 8-channel core-matrix columns (leading byte offset 8976 B) of [33][17]
-// 16-byte rows, with the x positions split by parity (9 even, then 8 odd) so
-// that every tap of the stride-2 convolution reads 8 consecutive rows: tap
-// (kz, ky, kx) of latent row (ly, lx) is h1 row 2 ly + ky, slot lx (kx = 0),
-// 9 + lx (kx = 1) or lx + 1 (kx = 2); 8-row groups (one per ly) are 544 B
-// apart.
+// E1 runs on the tensor cores as well: for each h1 plane, the warpgroup that
+// owns it (warpgroup 1 even planes, warpgroup 2 odd ones; three snapshot
+// slots, so that a warpgroup's next copy overlaps its current plane) writes
+// the bf16(s / rms) values of every h1 voxel's 2 x 2 x 2 patch as one row of
+// a 648-row A tile, the issuing thread runs 5 tcgen05.mma (M = 128 voxels,
+// N = 32, K = 16: the 8 patch values, then 8 columns multiplied by the zero
+// half of W1) into that warpgroup's 160 TMEM columns, and the warpgroup adds
+// b1, applies LeakyReLU, rounds to bf16 and stores h1 into a three-slot ring
+// laid out as E2's A operand in the canonical K-major no-swizzle layout:
+// four 8-channel core-matrix columns (leading byte offset 8976 B) of
+// [33][17] 16-byte rows, with the x positions split by parity (9 even, then
+// 8 odd) so that every tap of the stride-2 convolution reads 8 consecutive
+// rows: tap (kz, ky, kx) of latent row (ly, lx) is h1 row 2 ly + ky, slot lx
+// (kx = 0), 9 + lx (kx = 1) or lx + 1 (kx = 2); 8-row groups (one per ly)
+// are 544 B apart. The products, sums and rounding points are those of the
+// GEMM-engine encoder, so the latents are the same.
 //
 // E2 runs on the tensor cores, one h1 plane at a time: as soon as plane p is
 // complete, one thread issues its 9 taps x 2 tcgen05.mma (M = 128 latent
@@ -31,8 +35,9 @@
 // Two 16-column accumulators alternate between latent planes; warpgroup 3
 // adds b2, rounds to bf16 and stores the latent rows. The issuing thread runs
 // an event loop of non-blocking mbarrier tests (snapshot slot free -> next
-// copy; h1 plane complete and accumulator free -> its MMAs). mbarriers:
-// snapshot full (TMA bytes) / free (128 arrivals), h1 full (128 arrivals) /
+// copy; A tile built -> E1 MMAs; h1 plane complete and accumulator free ->
+// its E2 MMAs). mbarriers: snapshot full (TMA bytes) / free (128 arrivals),
+// A tile full (128 arrivals) / E1 done (commit), h1 full (128 arrivals) /
 // free (commit), accumulator full (commit) / free (128 arrivals). Every wait
 // is bounded and shares an abort flag.
 
@@ -60,12 +65,17 @@ constexpr int kH1Bytes = 35968;                          // 4 columns (35904 B),
 constexpr int SX = 40, SYR = 2 * HY;                     // snapshot box: 40 x 66 x 2
 constexpr int kSnapBytes = SX * SYR * 2 * 4;             // 21120
 constexpr int kW2Bytes = 54 * 512;                       // 27 taps x 2 halves of 16 x 16
-constexpr int kSS = 4, kSH = 3;
+constexpr int kSS = 3, kSH = 3;
 constexpr int kLook = 3;  // snapshot loads ahead of the next h1 plane to multiply
 constexpr long long kIdleLimit = 1LL << 26;  // producer loop turns without progress
-constexpr int kSmem = 128 + kW2Bytes + kSS * kSnapBytes + kSH * kH1Bytes;
+constexpr int kW1Bytes = 1024;      // W1 as a 32 x 16 operand (k 8..15 zero)
+constexpr int kARows = 648;         // E1 A tile: 5 M tiles of 128 rows + 8 rows read as K half 2
+constexpr int kATileBytes = kARows * 16;                 // 10368
+constexpr int kE1Col = 32;          // E1 accumulators: 2 x (5 x 32) TMEM columns from here
+constexpr int kSmem = 128 + kW2Bytes + kW1Bytes + kSS * kSnapBytes + kSH * kH1Bytes +
+                      2 * kATileBytes;
 constexpr int kThreads = 13 * 32;
-constexpr int kTmemCols = 32;
+constexpr int kTmemCols = 512;
 constexpr long long kLimit = 1LL << 24;
 
 struct Sched {
@@ -88,7 +98,6 @@ __device__ __forceinline__ void item_coords(const Sched& S, int lnz, int item, i
 }
 
 __device__ __forceinline__ float lrelu(float a) { return a > 0.f ? a : kSlope * a; }
-__device__ __forceinline__ float rbf(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
 
 __device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(b)),
@@ -192,15 +201,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                    const Sched S, int* status) {
     extern __shared__ uint8_t esm_raw[];
     __shared__ __align__(8) uint64_t snap_full[kSS], snap_free[kSS], h1_full[kSH], h1_free[kSH],
-        acc_full[2], acc_free[2], fin;
+        acc_full[2], acc_free[2], e1a_full[2], e1_done[2], fin;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
     uint8_t* base = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(esm_raw) + 127) & ~static_cast<uintptr_t>(127));
     uint8_t* w2 = base;
-    float* snap = reinterpret_cast<float*>(base + kW2Bytes);
-    uint8_t* h1 = base + kW2Bytes + kSS * kSnapBytes;
+    uint8_t* w1 = base + kW2Bytes;
+    float* snap = reinterpret_cast<float*>(w1 + kW1Bytes);
+    uint8_t* h1 = w1 + kW1Bytes + kSS * kSnapBytes;
+    uint8_t* atile = h1 + kSH * kH1Bytes;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int lnx = A.l.nx, lny = A.l.ny, lnz = A.l.nz;
@@ -218,6 +229,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int b = 0; b < 2; b++) {
             tc::mbar_init(&acc_full[b], 1);
             tc::mbar_init(&acc_free[b], 128);
+            tc::mbar_init(&e1a_full[b], 128);
+            tc::mbar_init(&e1_done[b], 1);
         }
         tc::mbar_init(&fin, 1);
         abort_flag = 0;
@@ -231,6 +244,20 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int e = 0; e < 8; e++) w[e] = A.P[kOW2 + o * 864 + tap * 32 + 16 * hh + 8 * j + e];
         *reinterpret_cast<uint4*>(w2 + t * 512 + b_off(o, 8 * j)) = tc::pack8(w);
+    }
+    // E1 B operand: W1[o][dz][dy][dx] as k = 0..7 of row o; k = 8..15 zero
+    if (tid < 64) {
+        const int o = tid >> 1, j = tid & 1;
+        float w[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) w[e] = j ? 0.f : A.P[kOW1 + o * 8 + e];
+        *reinterpret_cast<uint4*>(w1 + (o >> 3) * 256 + j * 128 + (o & 7) * 16) = tc::pack8(w);
+    }
+    // E1 A tiles: rows past the 561 voxels stay zero (the second K half of
+    // row r is row r + 8, multiplied by the zero half of W1, and must be finite)
+    for (int i = tid; i < 2 * (kARows - NVOX); i += kThreads) {
+        const int g = i / (kARows - NVOX), r = NVOX + i % (kARows - NVOX);
+        *reinterpret_cast<uint4*>(atile + g * kATileBytes + r * 16) = make_uint4(0u, 0u, 0u, 0u);
     }
     tc::fence_proxy_async();
     tc::tc_fence_before();
@@ -259,10 +286,29 @@ __global__ void __launch_bounds__(kThreads, 1)
             L.start(S, lnz);
             M.start(S, lnz);
             int l_seq = 0, mp = 0, obase = 0;
+            int e1_next[2] = {0, 1};  // next h1 plane of each E1 warpgroup
+            constexpr uint32_t idesc1 = tc::idesc_bf16(128, 32);
+            const uint64_t dW1 = tc::sdesc(tc::smem_u32(w1), 128, 256);
             long long idle = 0;
             bool ok = true;
             while (mp < np && ok) {
                 bool prog = false;
+#pragma unroll
+                for (int g = 0; g < 2; g++) {
+                    const int j = e1_next[g];
+                    if (j < np && test_bar(&e1a_full[g], (uint32_t)((j >> 1) & 1))) {
+                        // E1 of plane j: 5 M tiles of 128 voxels, K = 16 (8 inputs + 8 zeros)
+                        tc::tc_fence_after();
+                        const uint32_t a0 = tc::smem_u32(atile + g * kATileBytes);
+#pragma unroll
+                        for (int t = 0; t < 5; t++)
+                            tc::mma_bf16(tmem + kE1Col + g * 160 + t * 32,
+                                         tc::sdesc(a0 + t * 2048, 128, 128), dW1, idesc1, 0u);
+                        tc::mma_commit(&e1_done[g]);
+                        e1_next[g] = j + 2;
+                        prog = true;
+                    }
+                }
                 if (l_seq < np && l_seq <= mp + kLook) {
                     const int slot = l_seq % kSS;
                     if (l_seq < kSS || test_bar(&snap_free[slot], (uint32_t)((l_seq / kSS - 1) & 1))) {
@@ -321,15 +367,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp <= 8) {
         // ---------------- E1: two warpgroups, alternate h1 planes ----------------
-        const int g = (warp - 1) >> 2, t = tid - 32 - 128 * g;
-        const int kc = t & 3, vlane = t >> 2;  // 8-channel column, voxel lane (0..31)
-        float w[8][8], b1[8];
+        // per plane: A tile rows = bf16(s / rms) of each h1 voxel's 2 x 2 x 2 patch;
+        // the producer's MMAs put W1 x0 into this warpgroup's TMEM columns; the
+        // epilogue adds b1, applies LeakyReLU, rounds to bf16 and stores h1
+        const int g = (warp - 1) >> 2, t = tid - 32 - 128 * g, q = warp & 3;
+        uint8_t* at = atile + g * kATileBytes;
+        const uint32_t tcol = tmem + kE1Col + g * 160 + ((uint32_t)(q * 32) << 16);
+        float b1[32];
 #pragma unroll
-        for (int c = 0; c < 8; c++) {
-            b1[c] = A.P[kOB1 + 8 * kc + c];
-#pragma unroll
-            for (int d = 0; d < 8; d++) w[c][d] = rbf(A.P[kOW1 + (8 * kc + c) * 8 + d]);
-        }
+        for (int c = 0; c < 32; c++) b1[c] = A.P[kOB1 + c];
         const float inv_s = *A.inv_sigma;
         PlaneCursor C;
         C.start(S, lnz);
@@ -340,40 +386,56 @@ __global__ void __launch_bounds__(kThreads, 1)
             item_coords(S, lnz, C.item, cx, cy, z0, nz);
             const int hz = 2 * z0 - 1 + C.k;
             ok = wait_bar(&snap_full[j % kSS], (uint32_t)((j / kSS) & 1), abrt);
-            if (ok && j >= kSH) ok = wait_bar(&h1_free[j % kSH], (uint32_t)((j / kSH - 1) & 1), abrt);
             if (!ok) break;
             const float* sp = snap + (j % kSS) * (kSnapBytes / 4);
-            uint8_t* hp = h1 + (j % kSH) * kH1Bytes + kc * kKcBytes;
-            const bool zin = hz >= 0 && hz < A.h.nz;
-            for (int v = vlane; v < NVOX; v += 32) {
+            for (int v = t; v < NVOX; v += 128) {
                 const int iy = v / HX, ix = v - iy * HX;
-                const int hy = 32 * cy - 1 + iy, hx = 16 * cx - 1 + ix;
-                uint4 packed = make_uint4(0u, 0u, 0u, 0u);
-                if (zin && hy >= 0 && hy < A.h.ny && hx >= 0 && hx < A.h.nx) {
-                    float x[8];
+                float x[8];
 #pragma unroll
-                    for (int dz = 0; dz < 2; dz++)
+                for (int dz = 0; dz < 2; dz++)
 #pragma unroll
-                        for (int dy = 0; dy < 2; dy++) {
-                            const float2 p2 = *reinterpret_cast<const float2*>(
-                                sp + (dz * SYR + 2 * iy + dy) * SX + 2 + 2 * ix);
-                            x[dz * 4 + dy * 2] = rbf(p2.x * inv_s);
-                            x[dz * 4 + dy * 2 + 1] = rbf(p2.y * inv_s);
-                        }
-                    float hv[8];
-#pragma unroll
-                    for (int c = 0; c < 8; c++) {
-                        float acc = 0.f;
-#pragma unroll
-                        for (int d = 0; d < 8; d++) acc = fmaf(w[c][d], x[d], acc);
-                        hv[c] = lrelu(acc + b1[c]);
+                    for (int dy = 0; dy < 2; dy++) {
+                        const float2 p2 = *reinterpret_cast<const float2*>(
+                            sp + (dz * SYR + 2 * iy + dy) * SX + 2 + 2 * ix);
+                        x[dz * 4 + dy * 2] = p2.x * inv_s;
+                        x[dz * 4 + dy * 2 + 1] = p2.y * inv_s;
                     }
-                    packed = tc::pack8(hv);
-                }
-                *reinterpret_cast<uint4*>(hp + iy * kRowBytes + x_slot(ix) * 16) = packed;
+                *reinterpret_cast<uint4*>(at + v * 16) = tc::pack8(x);
             }
             tc::fence_proxy_async();
             bar_arrive(&snap_free[j % kSS]);
+            bar_arrive(&e1a_full[g]);
+            ok = wait_bar(&e1_done[g], (uint32_t)((j >> 1) & 1), abrt);
+            if (ok && j >= kSH) ok = wait_bar(&h1_free[j % kSH], (uint32_t)((j / kSH - 1) & 1), abrt);
+            if (!ok) break;
+            tc::tc_fence_after();
+            uint8_t* hp = h1 + (j % kSH) * kH1Bytes;
+            const bool zin = hz >= 0 && hz < A.h.nz;
+#pragma unroll 1
+            for (int mt = 0; mt < 5; mt++) {
+                const int v0 = mt * 128 + q * 32;
+                if (v0 >= NVOX) break;  // warp-uniform
+                float acc[32];
+                tc::tmem_ld16(tcol + mt * 32, acc);
+                tc::tmem_ld16(tcol + mt * 32 + 16, acc + 16);
+                const int v = v0 + lane;
+                if (v < NVOX) {
+                    const int iy = v / HX, ix = v - iy * HX;
+                    const int hy = 32 * cy - 1 + iy, hx = 16 * cx - 1 + ix;
+                    const bool in = zin && hy >= 0 && hy < A.h.ny && hx >= 0 && hx < A.h.nx;
+                    uint8_t* dst = hp + iy * kRowBytes + x_slot(ix) * 16;
+#pragma unroll
+                    for (int kc = 0; kc < 4; kc++) {
+                        float hv[8];
+#pragma unroll
+                        for (int c = 0; c < 8; c++) hv[c] = lrelu(acc[8 * kc + c] + b1[8 * kc + c]);
+                        *reinterpret_cast<uint4*>(dst + kc * kKcBytes) =
+                            in ? tc::pack8(hv) : make_uint4(0u, 0u, 0u, 0u);
+                    }
+                }
+            }
+            tc::tc_fence_before();
+            tc::fence_proxy_async();
             bar_arrive(&h1_full[j % kSH]);
         }
     } else {

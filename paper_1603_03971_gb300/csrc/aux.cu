@@ -149,6 +149,64 @@ __global__ void k_image_finalize(Geometry G, const float* __restrict__ slab,
     }
 }
 
+// source illumination: illum[z][y][x] += u^2 of the model columns of a
+// snapshot slab [nz][ny][NX]
+__global__ void k_illum_add(Geometry G, const float* __restrict__ slab,
+                            float* __restrict__ illum) {
+    const long long n = (long long)G.nx * G.ny * G.nz;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const long long zy = i / G.nx;
+        const int x = (int)(i % G.nx);
+        const float u = slab[zy * G.NX + x + G.nb];
+        illum[i] = fmaf(u, u, illum[i]);
+    }
+}
+
+// largest value of a non-negative array (float bits compare as unsigned)
+__global__ void k_max_nonneg(const float* __restrict__ a, long long n, unsigned int* bits) {
+    float m = 0.f;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        m = fmaxf(m, a[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(bits, __float_as_uint(m));
+}
+
+// out = image / (illum + eps_rel * max illum)
+__global__ void k_image_normalize(const float* __restrict__ image, const float* __restrict__ illum,
+                                  long long n, const unsigned int* max_bits, float eps_rel,
+                                  float* __restrict__ out) {
+    const float floor_ = eps_rel * __uint_as_float(*max_bits);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = image[i] / (illum[i] + floor_);
+}
+
+// out = -L image on the model grid, zero outside it; a[0] = 3 a0 / dx^2,
+// a[k] = a_k / dx^2
+__global__ void k_image_laplacian(const float* __restrict__ image, int nx, int ny, int nz,
+                                  LapWeights w, float* __restrict__ out) {
+    const long long n = (long long)nx * ny * nz;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long sy = nx, sz = (long long)nx * ny;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / sz);
+        float acc = w.a[0] * image[i];
+        for (int k = 1; k <= w.r; k++) {
+            float s = 0.f;
+            if (x + k < nx) s += image[i + k];
+            if (x - k >= 0) s += image[i - k];
+            if (y + k < ny) s += image[i + k * sy];
+            if (y - k >= 0) s += image[i - k * sy];
+            if (z + k < nz) s += image[i + k * sz];
+            if (z - k >= 0) s += image[i - k * sz];
+            acc = fmaf(w.a[k], s, acc);
+        }
+        out[i] = -acc;
+    }
+}
+
 __device__ __forceinline__ void fold_range(int m, int n, int nb, int N, int& lo, int& hi) {
     lo = (m == 0) ? 0 : m + nb;
     hi = (m == n - 1) ? N - 1 : m + nb;
@@ -255,6 +313,30 @@ cudaError_t launch_image_finalize(const Geometry& G, const float* slab, float* i
                                   cudaStream_t s) {
     const long long n = (long long)G.nx * G.ny * G.nz;
     k_image_finalize<<<grid_for(n, 256), 256, 0, s>>>(G, slab, image);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_illum_add(const Geometry& G, const float* slab, float* illum,
+                             cudaStream_t s) {
+    const long long n = (long long)G.nx * G.ny * G.nz;
+    k_illum_add<<<grid_for(n, 256), 256, 0, s>>>(G, slab, illum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_image_normalize(const float* image, const float* illum, long long n,
+                                   unsigned int* max_bits, float eps_rel, float* out,
+                                   cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(max_bits, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    k_max_nonneg<<<grid_for(n, 256), 256, 0, s>>>(illum, n, max_bits);
+    k_image_normalize<<<grid_for(n, 256), 256, 0, s>>>(image, illum, n, max_bits, eps_rel, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_image_laplacian(const float* image, int nx, int ny, int nz,
+                                   const LapWeights& w, float* out, cudaStream_t s) {
+    const long long n = (long long)nx * ny * nz;
+    k_image_laplacian<<<grid_for(n, 256), 256, 0, s>>>(image, nx, ny, nz, w, out);
     return cudaGetLastError();
 }
 

@@ -123,7 +123,8 @@ void count_launch(int n = 1) {
 
 // ---- workspace layout ----------------------------------------------------------
 constexpr size_t kAlign = 256;
-constexpr size_t kStatusBytes = 256;  // status word at 0, model-prep reduction at 16
+constexpr size_t kStatusBytes = 256;  // status word at 0, model-prep reduction at 16,
+                                      // image-filter maximum at 32
 size_t up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
@@ -269,10 +270,17 @@ struct Ctx {
     float inv_dx3;
     int variant;
     const float* ae = nullptr;  // codec parameters (learned storage)
+    float* illum = nullptr;     // source illumination, model grid (+=), or NULL
 
     float* at(size_t off) const { return reinterpret_cast<float*>(ws + off); }
     ae::bf16* latent_slot(size_t k) const {
         return reinterpret_cast<ae::bf16*>(ws + L.latent + k * L.latent_bytes);
+    }
+    // the model region of a padded field
+    ae::Vol field_view(float* f) const {
+        const long long NX = d.NX, NY = d.NY;
+        return ae::Vol{f + ((long long)p->nb * NY + p->nb) * NX + p->nb, NX, NX * NY, p->nx, p->ny,
+                       p->nz};
     }
     ae::Vol model_view(float* slab) const {
         return ae::Vol{slab + p->nb, (long long)d.NX, (long long)d.NX * p->ny, p->nx, p->ny, p->nz};
@@ -421,14 +429,12 @@ rtm_status run_forward(Ctx& C, const int32_t* rec, float* data, float* u_last) {
                 mode = MODE_FWD_SNAP;
                 snap = C.snap_slot((size_t)((n + 1) / ie - 1));
             }
-        } else if (p->storage == RTM_STORE_LEARNED && (n + 1) % ie == 0) {
-            mode = MODE_FWD_SNAP;
-            snap = C.snap_slot(0);
         }
         CHECK(stencil(C, mode, cur, prev, snap, nullptr));
         if (p->storage == RTM_STORE_LEARNED && (n + 1) % ie == 0) {
+            // the encoder reads u^{n+1} (now in prev) in place: no snapshot copy
             const size_t k = (size_t)((n + 1) / ie - 1);
-            CU(ae_encode(C.ae, C.model_view(snap), reinterpret_cast<ae::bf16*>(C.at(C.L.ae_h)),
+            CU(ae_encode(C.ae, C.field_view(prev), reinterpret_cast<ae::bf16*>(C.at(C.L.ae_h)),
                          C.latent_slot(k), reinterpret_cast<ae::AeScalars*>(C.at(C.L.ae_scalars)),
                          C.at(C.L.scales) + k, C.status(), C.s));
             count_launch(4);
@@ -470,6 +476,10 @@ rtm_status run_backward(Ctx& C, const int32_t* rec, const float* rdata, float* s
         else if (m % ie == 0) mode = MODE_BWD_IMAGE;
         CHECK(stencil(C, mode, mcur, mprev, mode == MODE_FWD ? nullptr : snap,
                       mode == MODE_FWD ? nullptr : acc));
+        if (mode == MODE_BWD_IMAGE && C.illum) {
+            CU(launch_illum_add(C.G, snap, C.illum, C.s));
+            count_launch();
+        }
         float* t = mprev;
         mprev = mcur;
         mcur = t;
@@ -734,6 +744,65 @@ rtm_status rtm_shot_learned(const rtm_params* p, const float* d_c, const int32_t
     CU(launch_image_finalize(C.G, C.at(C.L.img), d_image, C.s));
     count_launch();
     return finish(C);
+}
+
+rtm_status rtm_backward_image_illum(const rtm_params* p, const float* d_c, const int32_t* d_rec,
+                                    const float* d_rdata, const float* d_ae_params, void* d_ws,
+                                    size_t ws_bytes, float* d_image, float* d_illum,
+                                    rtm_stream stream) {
+    CHECK(common_checks(p, d_c, d_rec, d_ws, ws_bytes));
+    if (p->want_grad)
+        return fail(RTM_ERR_STATE, "workspace prepared for the gradient (want_grad = 1)");
+    if (p->storage == RTM_STORE_LEARNED && !d_ae_params)
+        return fail(RTM_ERR_INVALID, "learned storage needs the codec parameters");
+    if (!d_rdata && p->nrec > 0) return fail(RTM_ERR_INVALID, "receiver data is NULL");
+    if (!d_image || !d_illum) return fail(RTM_ERR_INVALID, "image or illumination is NULL");
+    Ctx C;
+    CHECK(make_ctx(C, p, d_c, d_ws, stream));
+    C.ae = d_ae_params;
+    C.illum = d_illum;
+    CHECK(run_backward(C, d_rec, d_rdata, nullptr, false));
+    CU(launch_image_finalize(C.G, C.at(C.L.img), d_image, C.s));
+    count_launch();
+    return finish(C);
+}
+
+rtm_status rtm_image_filter(const rtm_params* p, const float* d_image, const float* d_illum,
+                            float eps_rel, float* d_normalized, float* d_laplacian, void* d_ws,
+                            size_t ws_bytes, rtm_stream stream) {
+    // only the model grid, the radius and dx matter here
+    if (!p) return fail(RTM_ERR_INVALID, "params is NULL");
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1)
+        return fail(RTM_ERR_INVALID, "model grid %dx%dx%d must be positive", p->nx, p->ny, p->nz);
+    if (p->radius != 4 && p->radius != 8)
+        return fail(RTM_ERR_UNSUPPORTED, "stencil radius %d (4 or 8 supported)", p->radius);
+    if (!(p->dx > 0.0) || !isfinite(p->dx)) return fail(RTM_ERR_INVALID, "dx must be positive");
+    if (!d_image) return fail(RTM_ERR_INVALID, "image is NULL");
+    if (d_normalized && (!d_illum || !(eps_rel > 0.f)))
+        return fail(RTM_ERR_INVALID, "normalisation needs the illumination and eps_rel > 0");
+    if (d_normalized && (!d_ws || ws_bytes < kStatusBytes))
+        return fail(RTM_ERR_WORKSPACE, "normalisation needs a workspace (its status block)");
+    cudaGetLastError();
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const long long n = (long long)p->nx * p->ny * p->nz;
+    if (d_normalized) {
+        unsigned int* bits = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(d_ws) + 32);
+        CU(launch_image_normalize(d_image, d_illum, n, bits, eps_rel, d_normalized, s));
+        count_launch(2);
+    }
+    if (d_laplacian) {
+        LapWeights w;
+        memset(&w, 0, sizeof w);
+        double a[kMaxRadius + 1];
+        weights(p->radius, a);
+        const double inv_dx2 = 1.0 / (p->dx * p->dx);
+        w.r = p->radius;
+        w.a[0] = (float)(3.0 * a[0] * inv_dx2);
+        for (int k = 1; k <= p->radius; k++) w.a[k] = (float)(a[k] * inv_dx2);
+        CU(launch_image_laplacian(d_image, p->nx, p->ny, p->nz, w, d_laplacian, s));
+        count_launch();
+    }
+    return RTM_OK;
 }
 
 rtm_status rtm_snapshot(const rtm_params* p, const void* d_ws, size_t ws_bytes, int32_t m,

@@ -78,6 +78,18 @@ cudaError_t launch_grad_finalize(const Geometry& G, const float* acc, const floa
                                  double dx3, double dt2, float* grad_v2, cudaStream_t s);
 cudaError_t launch_misfit(const float* d, const float* obs, long long n, float* resid,
                           double* J, cudaStream_t s);
+// imaging-condition variants: source illumination (+= u^2 of a snapshot
+// slab's model columns), illumination-normalised image, Laplacian filter
+struct LapWeights {
+    int r;
+    float a[kMaxRadius + 1];  // a[0] = 3 a0 / dx^2, a[k] = a_k / dx^2
+};
+cudaError_t launch_illum_add(const Geometry& G, const float* slab, float* illum, cudaStream_t s);
+cudaError_t launch_image_normalize(const float* image, const float* illum, long long n,
+                                   unsigned int* max_bits, float eps_rel, float* out,
+                                   cudaStream_t s);
+cudaError_t launch_image_laplacian(const float* image, int nx, int ny, int nz,
+                                   const LapWeights& w, float* out, cudaStream_t s);
 
 // sets the thread-local message of rtm_last_error() and returns code
 int set_error(int code, const char* fmt, ...);

@@ -10,7 +10,7 @@ from __future__ import annotations
 
 import math
 import time
-from typing import List, Optional
+from typing import Optional
 
 import numpy as np
 import torch
@@ -31,7 +31,10 @@ def training_snapshots(n_models: int = 64, size: int = 192, nb: int = 32, nt: in
     snapshots at the multiples of ``every`` from ``first`` to ``nt``."""
     dt = rtm_inputs.courant_dt(dx, vmax)
     rng = np.random.Generator(np.random.PCG64(seed0))
-    out: List[torch.Tensor] = []
+    steps = list(range(every * max(1, -(-first // every)), nt + 1, every))
+    out = torch.empty((n_models * len(steps), size, size, size), dtype=torch.float32,
+                      device=device)
+    k = 0
     for i in range(n_models):
         src = (int(rng.integers(size // 4, 3 * size // 4)),
                int(rng.integers(size // 4, 3 * size // 4)), 4)
@@ -43,10 +46,11 @@ def training_snapshots(n_models: int = 64, size: int = 192, nb: int = 32, nt: in
         c = model_prep(p, v.contiguous(), ws)
         rec = torch.tensor([[size // 2, size // 2, 2]], dtype=torch.int32, device=device)
         forward(p, c, rec, ws)
-        for m in range(every * max(1, -(-first // every)), nt + 1, every):
-            out.append(snapshot(p, ws, m).clone())
+        for m in steps:
+            snapshot(p, ws, m, out=out[k])
+            k += 1
         del ws, c, v
-    return torch.stack(out)
+    return out
 
 
 def train(data: torch.Tensor, steps: int = 1500, batch: int = 4, lr: float = 1e-3,

@@ -142,6 +142,25 @@ def blob_perturbation(v, amplitude: float = 0.05, radius: float = 16.0,
     return v * torch.from_numpy(bump.astype(np.float32)).to(v.device)
 
 
+def thin_bed_reflectors(v, depths=(96, 192, 288), thickness: int = 8,
+                       contrast: float = 0.08):
+    """``v`` with thin horizontal beds: at each model depth index in
+    ``depths`` a bed of ``thickness`` cells whose velocity is scaled by
+    ``1 + contrast`` (alternating in sign from bed to bed). Reflections from
+    their top and bottom edges make the scattered data that an RTM images.
+    Works on numpy arrays and torch tensors."""
+    nz = v.shape[0]
+    scale = np.ones(nz, dtype=np.float64)
+    for i, d in enumerate(depths):
+        sign = 1.0 if i % 2 == 0 else -1.0
+        scale[max(0, d):min(nz, d + thickness)] = 1.0 + sign * contrast
+    if isinstance(v, np.ndarray):
+        return v * scale.astype(v.dtype)[:, None, None]
+    import torch
+
+    return v * torch.from_numpy(scale.astype(np.float32)).to(v.device)[:, None, None]
+
+
 def layered_salt_velocity(nx: int, ny: int, nz: int, seed: int = 4,
                           n_layers: int = 5, v_first: float = 1500.0,
                           v_last: float = 4000.0, n_bodies: int = 6,

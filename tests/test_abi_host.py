@@ -106,6 +106,21 @@ def test_calls_reject_bad_arguments_without_a_device():
     assert L.rtm_ae_set_decoder(0) == 0
     assert L.rtm_ae_set_encoder(3) == 1
     assert L.rtm_ae_set_encoder(0) == 0
+    # imaging variants: illumination output required; filter argument checks
+    assert L.rtm_backward_image_illum(ctypes.byref(p), fake, fake, fake, None, fake, n, fake,
+                                      None, None) == 1
+    assert L.rtm_image_filter(ctypes.byref(p), None, fake, ctypes.c_float(1e-3), fake, None,
+                              fake, 256, None) == 1
+    assert L.rtm_image_filter(ctypes.byref(p), fake, None, ctypes.c_float(1e-3), fake, None,
+                              fake, 256, None) == 1
+    assert L.rtm_image_filter(ctypes.byref(p), fake, fake, ctypes.c_float(0.0), fake, None,
+                              fake, 256, None) == 1
+    assert L.rtm_image_filter(ctypes.byref(p), fake, fake, ctypes.c_float(1e-3), fake, None,
+                              fake, 8, None) == 3
+    p6 = _p()
+    p6.radius = 6
+    assert L.rtm_image_filter(ctypes.byref(p6), fake, None, ctypes.c_float(1e-3), None, fake,
+                              None, 0, None) == 7
 
 
 def test_workspace_sizes_follow_the_storage_policy():

@@ -1,15 +1,17 @@
 """Learned snapshot storage: the RTM image built from autoencoder-compressed
 source snapshots.
 
-1. Parity: the GPU learned shot equals the oracle's receiver propagation and
-   imaging fed with the snapshots that the GPU codec reconstructs (the codec
-   itself is checked in test_gpu_codec.py), within the wavefield tolerance.
+1. Parity: the GPU learned shot against the oracle chain computed end to
+   end in FP64 on the CPU (propagation, codec with bfloat16 rounding at the
+   GPU's storage points, receiver propagation and imaging). The image is
+   linear in the decoded snapshots, so the codec tolerance (2e-3) bounds it.
 2. Gain: a codec trained (by the library's own kernels) on snapshots the
    propagator generated from other random models reconstructs and images
    far closer to the exact snapshots and image than the untrained network.
-   The non-learned 8x baseline (decimation by 2 per axis + linear
-   interpolation) is printed beside them; at this training budget it is
-   not beaten, and the test does not claim it.
+   All images here are the GPU's own (store-all vs learned storage); the
+   non-learned 8x baseline (decimation by 2 per axis + linear
+   interpolation) is printed beside them at the snapshot level; at this
+   training budget it is not beaten, and the test does not claim it.
 """
 import numpy as np
 import pytest
@@ -18,72 +20,60 @@ import rtm_inputs
 from helpers import Case, rel_l2
 
 pytestmark = pytest.mark.gpu
+CODEC_TOL = 2e-3
 
 
-def _store_all_snapshots(case, ie):
-    import torch
-
-    import paper_1603_03971_gb300 as rtm
-    from helpers import GpuRun
-
-    g = GpuRun(case)
-    g.forward()
-    snaps = {m: rtm.snapshot(g.p, g.ws, m).clone() for m in range(ie, case.nt + 1, ie)}
-    torch.cuda.synchronize()
-    return g, snaps
-
-
-def _oracle_image(case, d_obs, snaps_np, ie):
-    prob = case.oracle_problem()
-    su = np.zeros((case.nt, case.nz, case.ny, case.nx))
-    for m, s in snaps_np.items():
-        su[m - 1] = s
-    return prob.grid.adjoint(prob.w, prob.src, prob.rec, d_obs, snap_u=su, image_every=ie)["image"]
-
-
-def _decode_all(P, snaps, shape):
-    from paper_1603_03971_gb300 import codec
-
-    ws = codec.alloc_workspace(shape)
-    out = {}
-    for m, s in snaps.items():
-        lat, sc = codec.encode(P, s, ws)
-        out[m] = codec.decode(P, lat, sc, ws).cpu().numpy().astype(np.float64)
-    return out
-
-
-def test_learned_shot_matches_oracle_on_reconstructed_snapshots():
+def _learned_image(case, g, P, d_obs_np):
     import torch
 
     import paper_1603_03971_gb300 as rtm
 
-    ie = 4
-    case = Case(nx=32, ny=28, nz=24, nb=8, r=4, nt=40, image_every=ie)
-    g, snaps = _store_all_snapshots(case, ie)
-    P = torch.from_numpy(rtm_inputs.ae_flat(rtm_inputs.ae_init_params(2)).astype(np.float32)).cuda()
-    d_obs = case.d_obs(g.nrec)
-    dobs = torch.from_numpy(d_obs.astype(np.float32)).cuda()
     pl = case.params()
     pl.storage = 2  # RTM_STORE_LEARNED
     wl = rtm.alloc_workspace(pl)
+    dobs = torch.from_numpy(np.ascontiguousarray(d_obs_np, dtype=np.float32)).cuda()
     img = torch.zeros((case.nz, case.ny, case.nx), device="cuda")
     rtm.shot_learned(pl, g.c, g.rec, dobs, P, wl, img)
     rtm.check(wl)
-    rec_snaps = _decode_all(P, snaps, (case.nz, case.ny, case.nx))
-    ref = _oracle_image(case, d_obs, rec_snaps, ie)
-    assert rel_l2(img.cpu().numpy(), ref) <= 1e-4
+    return img.cpu().numpy().astype(np.float64)
+
+
+def test_learned_shot_matches_the_oracle_chain():
+    import torch
+
+    from helpers import GpuRun
+    from oracle import ae as oae
+
+    ie = 4
+    case = Case(nx=32, ny=28, nz=24, nb=8, r=4, nt=40, image_every=ie)
+    P = rtm_inputs.ae_flat(rtm_inputs.ae_init_params(2)).astype(np.float32)
+    g = GpuRun(case)
+    d_obs = case.d_obs(g.nrec)
+    img = _learned_image(case, g, torch.from_numpy(P).cuda(), d_obs)
+    # oracle: snapshots, codec and imaging, all on the CPU
+    prob = case.oracle_problem()
+    fw = prob.forward(keep_u=True)
+    params = oae.unflatten(P.astype(np.float64))
+    su = np.zeros_like(fw["u"])
+    for m in range(ie, case.nt + 1, ie):
+        lat, sc = oae.encode(params, fw["u"][m - 1].astype(np.float32).astype(np.float64))
+        su[m - 1] = oae.decode(params, lat, sc)
+    ref = prob.grid.adjoint(prob.w, prob.src, prob.rec, d_obs, snap_u=su,
+                            image_every=ie)["image"]
+    assert rel_l2(img, ref) <= CODEC_TOL
 
 
 def test_trained_codec_beats_the_untrained_network():
     """The codec's gain from training: trained on snapshots of 16 other random
     models, it reconstructs held-out snapshots far better than the same
-    network untrained, and its RTM image is correspondingly closer to the
-    exact image. The non-learned 8x baseline (decimation by 2 per axis +
-    linear interpolation) is printed beside them for reference."""
+    network untrained, and its RTM image (learned storage) is
+    correspondingly closer to the store-all image."""
     import torch
 
+    from helpers import GpuRun
     from oracle import ae as oae
-    from paper_1603_03971_gb300 import learned
+    import paper_1603_03971_gb300 as rtm
+    from paper_1603_03971_gb300 import codec, learned
 
     n = 96
     data = learned.training_snapshots(n_models=16, size=n, nb=16, nt=640, every=20, first=40,
@@ -94,30 +84,36 @@ def test_trained_codec_beats_the_untrained_network():
     ie = 8
     case = Case(nx=n, ny=n, nz=n, nb=16, r=4, nt=480, image_every=ie, f0=20.0, t0=0.05,
                 vmax=4500.0, src=(48, 40, 4), rec_stride=3, seed=77, sigma=8.0)
-    g, snaps = _store_all_snapshots(case, ie)
-    d_obs = g.forward()[0].cpu().numpy().astype(np.float64)
-    exact = {m: s.cpu().numpy().astype(np.float64) for m, s in snaps.items()}
+    g = GpuRun(case)
+    g.forward()
+    exact = {m: rtm.snapshot(g.p, g.ws, m).clone() for m in range(ie, case.nt + 1, ie)}
+    d_obs = case.d_obs(g.nrec)
+    img_exact = g.backward_image(d_obs)[0].cpu().numpy().astype(np.float64)
     P0 = torch.from_numpy(rtm_inputs.ae_flat(rtm_inputs.ae_init_params(1)).astype(np.float32)).cuda()
-    rec_tr = _decode_all(P, snaps, (n, n, n))
-    rec_un = _decode_all(P0, snaps, (n, n, n))
-    rec_de = {m: oae.trilinear_upsample(oae.decimate(s), n) for m, s in exact.items()}
+    ws = codec.alloc_workspace((n, n, n))
 
-    def snap_err(rec):
-        num = sum(float(np.sum((rec[m] - exact[m]) ** 2)) for m in exact)
-        return (num / sum(float(np.sum(exact[m] ** 2)) for m in exact)) ** 0.5
+    def snap_err(params):
+        num = den = 0.0
+        for s in exact.values():
+            lat, sc = codec.encode(params, s, ws)
+            r = codec.decode(params, lat, sc, ws)
+            num += float(((r - s).double() ** 2).sum())
+            den += float((s.double() ** 2).sum())
+        return (num / den) ** 0.5
 
-    e_tr, e_un, e_de = snap_err(rec_tr), snap_err(rec_un), snap_err(rec_de)
-    img = {k: _oracle_image(case, d_obs, r, ie)
-           for k, r in (("exact", exact), ("trained", rec_tr), ("untrained", rec_un),
-                        ("decimation", rec_de))}
-    ie_tr = rel_l2(img["trained"], img["exact"])
-    ie_un = rel_l2(img["untrained"], img["exact"])
-    ie_de = rel_l2(img["decimation"], img["exact"])
+    e_tr, e_un = snap_err(P), snap_err(P0)
+    num = den = 0.0
+    for s in exact.values():  # printed reference only
+        sn = s.cpu().numpy().astype(np.float64)
+        num += float(np.sum((oae.trilinear_upsample(oae.decimate(sn), n) - sn) ** 2))
+        den += float(np.sum(sn ** 2))
+    e_de = (num / den) ** 0.5
+    img = {"trained": _learned_image(case, g, P, d_obs), "untrained": _learned_image(case, g, P0, d_obs)}
+    ie_tr, ie_un = (rel_l2(img[k], img_exact) for k in ("trained", "untrained"))
     deep = slice(8, None)
-    dd = {k: rel_l2(img[k][deep], img["exact"][deep]) for k in ("trained", "untrained",
-                                                                  "decimation")}
+    dd = {k: rel_l2(img[k][deep], img_exact[deep]) for k in img}
     print("snapshot rel-L2: trained %.3e untrained %.3e decimation %.3e" % (e_tr, e_un, e_de))
-    print("image rel-L2: trained %.3e untrained %.3e decimation %.3e" % (ie_tr, ie_un, ie_de))
+    print("image rel-L2: trained %.3e untrained %.3e" % (ie_tr, ie_un))
     print("image rel-L2 below z=8: %s" % {k: round(v, 4) for k, v in dd.items()})
     assert e_tr < 0.25 * e_un
     assert ie_tr < 0.6 * ie_un
