@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--imaging", action="store_true",
                     help="also time the imaging-condition variants (source illumination, "
                          "normalised and Laplacian-filtered image) on the main workload")
+    ap.add_argument("--revolve", type=int, default=0, metavar="SLOTS",
+                    help="also time one shot of the main workload with binomial checkpointing "
+                         "in SLOTS checkpoint slots")
     ap.add_argument("--variant", type=int, default=0,
                     help="stencil plane-load variant: 0 automatic, 1 vector loads, 2 TMA")
     return ap.parse_args()
@@ -390,6 +393,37 @@ def imaging_leg(p, c, rec, dobs, ws, dev):
             "filter_s": t_filter}
 
 
+def revolve_leg(w, slots, vel, rec, dobs, dev):
+    """One shot of the main workload with binomial checkpointing in ``slots``
+    slots (the forward pass models data only; the backward pass recomputes
+    along the optimal schedule), CUDA events around the shot."""
+    import torch
+
+    import paper_1603_03971_gb300 as rtm
+
+    p = rtm.params_for(w, storage="revolve", ckpt_every=slots)
+    ws = rtm.alloc_workspace(p, dev)
+    c = rtm.model_prep(p, vel, ws)
+    img = torch.zeros((p.nz, p.ny, p.nx), dtype=torch.float32, device=dev)
+    rtm.shot(p, c, rec, dobs, ws, img)  # warm-up (and the schedule's plan)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    rtm.shot(p, c, rec, dobs, ws, img)
+    ev[1].record()
+    torch.cuda.synchronize()
+    rtm.check(ws)
+    t = ev[0].elapsed_time(ev[1]) / 1e3
+    nrecomp = rtm.revolve_cost(p.nt // p.image_every, slots) * p.image_every
+    NZ, NY, NX = w.padded_shape
+    steps = p.nt + nrecomp + p.nt  # data forward + recompute + backward
+    res = {"slots": slots, "workspace_gb": ws.numel() / 1e9, "shot_s": t,
+           "recomputed_forward_steps": nrecomp, "stencil_steps": steps,
+           "gpoint_updates_per_s": steps * NX * NY * NZ / t / 1e9}
+    del ws
+    return res
+
+
 def batch_leg(args, dev):
     """32 shots on seeded uneven apertures of a 1024 x 1024 x 512 layered /
     salt model, radius-8 stencil, each a full checkpointed RTM, in one
@@ -547,6 +581,9 @@ def run_ours(args):
     imaging_res = None
     if rank == 0 and args.imaging:
         imaging_res = imaging_leg(p, c, rec, dobs, ws, dev)
+    revolve_res = None
+    if rank == 0 and args.revolve > 0:
+        revolve_res = revolve_leg(w, args.revolve, vel, rec, dobs, dev)
     del vel
     learned = None
     if rank == 0 and not args.no_learned:
@@ -579,7 +616,7 @@ def run_ours(args):
             "config": cfg, "shot_s": t_max / args.steps, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": st["launches"],
             "clocks": clocks, "impl": "ours", "learned": learned, "batch": batch_res,
-            "imaging": imaging_res,
+            "imaging": imaging_res, "revolve": revolve_res,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

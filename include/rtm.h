@@ -67,7 +67,7 @@ typedef enum {
     RTM_ERR_STATE = 8        /* workspace prepared for another purpose */
 } rtm_status;
 
-enum { RTM_STORE_ALL = 0, RTM_STORE_CKPT = 1, RTM_STORE_LEARNED = 2 };
+enum { RTM_STORE_ALL = 0, RTM_STORE_CKPT = 1, RTM_STORE_LEARNED = 2, RTM_STORE_REVOLVE = 3 };
 enum { RTM_VEL_V = 0, RTM_VEL_V2 = 1 };
 
 typedef struct {
@@ -84,8 +84,11 @@ typedef struct {
     int32_t storage;        /* RTM_STORE_ALL: keep every imaging snapshot;
                                RTM_STORE_CKPT: checkpoints + segment recompute;
                                RTM_STORE_LEARNED: an 8x autoencoder latent per
-                               imaging snapshot (the *_learned calls) */
-    int32_t ckpt_every;     /* steps per checkpoint segment (RTM_STORE_CKPT) */
+                               imaging snapshot (the *_learned calls);
+                               RTM_STORE_REVOLVE: binomial checkpointing in a
+                               fixed number of slots (imaging only) */
+    int32_t ckpt_every;     /* steps per checkpoint segment (RTM_STORE_CKPT);
+                               number of checkpoint slots (RTM_STORE_REVOLVE) */
     int32_t image_every;    /* image at steps m with m % image_every == 0 (>= 1) */
     int32_t want_grad;      /* 1: prepare the workspace for rtm_grad instead of imaging */
 } rtm_params;
@@ -278,6 +281,30 @@ rtm_status rtm_ae_set_encoder(int32_t which);
  * 32. A bounded wait that runs out writes RTM_ERR_TIMEOUT to *d_status. */
 rtm_status rtm_ae_gemm_bf16(const uint16_t *d_A, const uint16_t *d_B, float *d_C, int32_t M,
                             int32_t K, int32_t N, int32_t *d_status, rtm_stream stream);
+
+/* ---- binomial checkpointing (RTM_STORE_REVOLVE) ----------------------------
+ * The receiver pass needs the source wavefield at the imaging steps in
+ * reverse order. With s = p->ckpt_every slots, each holding a leapfrog pair
+ * (2 padded fields), the backward call recomputes the source states from the
+ * zero initial state and the slots along the schedule with the fewest
+ * forward steps T(n, s), n = nt / image_every imaging steps:
+ *   T(0, s) = 0, T(n, 0) = n (n + 1) / 2,
+ *   T(n, s) = min_{1 <= c <= n} [c + T(n - c, s - 1) + T(c - 1, s)],
+ * in units of image_every forward steps (the recursion of binomial, or
+ * revolve, checkpointing; the forward call stores nothing and only models
+ * the data). Memory: s slots + one snapshot slab, independent of nt. The
+ * planning table is O(n^2 s) host work, refused beyond n^2 s = 2e9.
+ *
+ * rtm_revolve_cost: T(n, s) in image_every-step units (-1 over the limit).
+ * rtm_revolve_schedule: the action list into h_actions (host memory, 4
+ * int32 per action: op, a, b, c; op 0 restore slot a (-1: zero state) holding
+ * state b, 1 advance from state a to state b (c = 1: write the snapshot at
+ * the end), 2 store state b in slot a, 3 deliver state a (b = -1: the working
+ * pair, b >= 0: from slot b), 4 free slot a). Returns the number of actions;
+ * if that exceeds max_actions nothing is written; -1 over the limit. */
+int64_t rtm_revolve_cost(int32_t nstates, int32_t slots);
+int32_t rtm_revolve_schedule(int32_t nstates, int32_t slots, int32_t *h_actions,
+                             int32_t max_actions);
 
 /* ---- imaging-condition variants -------------------------------------------
  * The paper forms the image by zero-lag cross-correlation of the source and

@@ -16,7 +16,8 @@ from typing import Optional
 
 import torch
 
-from ._lib import (RTM_STORE_ALL, RTM_STORE_CKPT, RTM_STORE_LEARNED, RTM_VEL_V, RTM_VEL_V2,
+from ._lib import (RTM_STORE_ALL, RTM_STORE_CKPT, RTM_STORE_LEARNED, RTM_STORE_REVOLVE,
+                   RTM_VEL_V, RTM_VEL_V2,
                    RtmError, RtmParams, RtmStats, call, lib)
 
 __all__ = [
@@ -40,7 +41,7 @@ def make_params(nx, ny, nz, nb, radius, nt, dx, dt, f0, t0, src, nrec, storage="
     p.src_x, p.src_y, p.src_z = (int(v) for v in src)
     p.nrec = int(nrec)
     p.storage = {"all": RTM_STORE_ALL, "ckpt": RTM_STORE_CKPT,
-                 "learned": RTM_STORE_LEARNED}[storage]
+                 "learned": RTM_STORE_LEARNED, "revolve": RTM_STORE_REVOLVE}[storage]
     p.ckpt_every = int(ckpt_every)
     p.image_every = int(image_every)
     p.want_grad = 1 if want_grad else 0
@@ -243,6 +244,22 @@ def shot_host(p: RtmParams, vel, rec, dobs, image, ws, kind="v", stream=None):
          _host(dobs, torch.float32, "dobs"), _host(image, torch.float32, "image"), w, wb,
          _stream(stream))
     return image
+
+
+def revolve_cost(nstates: int, slots: int) -> int:
+    """Fewest forward steps (in image_every units) of binomial checkpointing
+    with ``slots`` checkpoint slots over ``nstates`` imaging steps."""
+    return int(lib().rtm_revolve_cost(int(nstates), int(slots)))
+
+
+def revolve_schedule(nstates: int, slots: int):
+    """The binomial checkpointing actions as a list of (op, a, b, c)."""
+    n = int(lib().rtm_revolve_schedule(int(nstates), int(slots), None, 0))
+    if n < 0:
+        raise ValueError("schedule over the planning limit")
+    buf = (ctypes.c_int32 * (4 * max(n, 1)))()
+    lib().rtm_revolve_schedule(int(nstates), int(slots), ctypes.cast(buf, ctypes.c_void_p), n)
+    return [tuple(buf[4 * i:4 * i + 4]) for i in range(n)]
 
 
 def set_tuning(radius: int, zchunk: int = 0, variant: int = 0):

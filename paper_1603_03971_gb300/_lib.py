@@ -16,7 +16,7 @@ STATUS_NAMES = {
     4: "RTM_ERR_CUDA", 5: "RTM_ERR_TIMEOUT", 6: "RTM_ERR_NUMERIC", 7: "RTM_ERR_UNSUPPORTED",
     8: "RTM_ERR_STATE",
 }
-RTM_STORE_ALL, RTM_STORE_CKPT, RTM_STORE_LEARNED = 0, 1, 2
+RTM_STORE_ALL, RTM_STORE_CKPT, RTM_STORE_LEARNED, RTM_STORE_REVOLVE = 0, 1, 2, 3
 RTM_VEL_V, RTM_VEL_V2 = 0, 1
 
 
@@ -90,6 +90,8 @@ SIGNATURES = {
     "rtm_backward_image_illum": (ctypes.c_int, [_P, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _vp,
                                                 _vp]),
     "rtm_image_filter": (ctypes.c_int, [_P, _vp, _vp, ctypes.c_float, _vp, _vp, _vp, _sz, _vp]),
+    "rtm_revolve_cost": (ctypes.c_int64, [_i32, _i32]),
+    "rtm_revolve_schedule": (ctypes.c_int32, [_i32, _i32, _vp, _i32]),
     "rtm_ae_param_count": (_sz, []),
     "rtm_ae_workspace_size": (_sz, [_i32, _i32, _i32]),
     "rtm_ae_encode": (ctypes.c_int, [_vp, _vp, _i64, _i64, _i32, _i32, _i32, _vp, _vp, _vp, _sz,

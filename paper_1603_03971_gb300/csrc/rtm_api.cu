@@ -13,6 +13,7 @@
 
 #include "../../include/rtm.h"
 #include "ae_internal.h"
+#include "revolve.h"
 #include "rtm_internal.h"
 
 using namespace rtm;
@@ -190,6 +191,11 @@ Layout layout_of(const rtm_params* p) {
         L.nsnap = 1;  // one snapshot slab, encoded or decoded in place
     } else if (p->storage == RTM_STORE_ALL) {
         L.nsnap = p->want_grad ? (size_t)p->nt : (size_t)(p->nt / p->image_every);
+    } else if (p->storage == RTM_STORE_REVOLVE) {
+        const int M = p->nt / (p->image_every > 0 ? p->image_every : 1);
+        L.nckpt = (size_t)(p->ckpt_every < M ? p->ckpt_every : M);
+        L.ckpt = take(2 * fb * L.nckpt);
+        L.nsnap = 1;  // the snapshot of the state being delivered
     } else {
         const int k = p->ckpt_every;
         const int nseg = (p->nt + k - 1) / k;
@@ -228,8 +234,17 @@ rtm_status validate(const rtm_params* p) {
                     p->src_y, p->src_z);
     if (p->nrec < 0) return fail(RTM_ERR_INVALID, "nrec %d < 0", p->nrec);
     if (p->storage != RTM_STORE_ALL && p->storage != RTM_STORE_CKPT &&
-        p->storage != RTM_STORE_LEARNED)
+        p->storage != RTM_STORE_LEARNED && p->storage != RTM_STORE_REVOLVE)
         return fail(RTM_ERR_INVALID, "storage %d unknown", p->storage);
+    if (p->storage == RTM_STORE_REVOLVE) {
+        if (p->want_grad)
+            return fail(RTM_ERR_INVALID, "binomial checkpointing serves imaging, not the gradient");
+        if (p->ckpt_every < 0) return fail(RTM_ERR_INVALID, "checkpoint slots %d < 0", p->ckpt_every);
+        if (p->image_every >= 1 && revolve_cost(p->nt / p->image_every, p->ckpt_every) < 0)
+            return fail(RTM_ERR_UNSUPPORTED,
+                        "binomial schedule for %d imaging steps and %d slots exceeds the planning limit",
+                        p->nt / p->image_every, p->ckpt_every);
+    }
     if (p->storage == RTM_STORE_LEARNED) {
         if (p->nx % 4 || p->ny % 4 || p->nz % 4)
             return fail(RTM_ERR_INVALID, "learned storage needs model sides that are multiples of 4");
@@ -452,6 +467,80 @@ rtm_status run_forward(Ctx& C, const int32_t* rec, float* data, float* u_last) {
     return RTM_OK;
 }
 
+// binomial checkpointing: the source states the imaging steps need, in
+// reverse order, from a schedule of forward recomputation, slot stores and
+// restores (revolve.h); backward steps run as their states are delivered
+template <class BackStep>
+rtm_status run_revolve(Ctx& C, const int32_t* rec, BackStep& back_step) {
+    const rtm_params* p = C.p;
+    const int ie = p->image_every;
+    const int M = p->nt / ie;
+    std::vector<RevolveAction> plan;
+    if (!revolve_schedule(M, p->ckpt_every, plan))
+        return fail(RTM_ERR_UNSUPPORTED, "binomial schedule over the planning limit");
+    const size_t fb = sizeof(float) * C.d.N;
+    float* fp = C.at(C.L.f[0]);  // u^{n-1} of the working pair
+    float* fc = C.at(C.L.f[1]);  // u^n
+    float* slab = C.snap_slot(0);
+    const size_t row = sizeof(float) * (size_t)p->ny * C.d.NX;  // model rows of one plane
+    int m_next = p->nt;  // next backward step
+    for (const RevolveAction& A : plan) {
+        switch (A.op) {
+            case REV_RESTORE:
+                if (A.a < 0) {
+                    CU(cudaMemsetAsync(fp, 0, fb, C.s));
+                    CU(cudaMemsetAsync(fc, 0, fb, C.s));
+                } else {
+                    CU(cudaMemcpyAsync(fp, C.ckpt_field((size_t)A.a + 1, 0), fb,
+                                       cudaMemcpyDeviceToDevice, C.s));
+                    CU(cudaMemcpyAsync(fc, C.ckpt_field((size_t)A.a + 1, 1), fb,
+                                       cudaMemcpyDeviceToDevice, C.s));
+                }
+                break;
+            case REV_ADVANCE:
+                for (int n = A.a * ie; n < A.b * ie; n++) {
+                    CHECK(fwd_aux(C, fc, fp, rec, nullptr, C.wav() + n));
+                    const bool snap = A.c && n == A.b * ie - 1;
+                    CHECK(stencil(C, snap ? MODE_FWD_SNAP : MODE_FWD, fc, fp, snap ? slab : nullptr,
+                                  nullptr));
+                    float* t = fp;
+                    fp = fc;
+                    fc = t;
+                }
+                break;
+            case REV_STORE:
+                CU(cudaMemcpyAsync(C.ckpt_field((size_t)A.a + 1, 0), fp, fb,
+                                   cudaMemcpyDeviceToDevice, C.s));
+                CU(cudaMemcpyAsync(C.ckpt_field((size_t)A.a + 1, 1), fc, fb,
+                                   cudaMemcpyDeviceToDevice, C.s));
+                break;
+            case REV_DELIVER: {
+                const int m_img = A.a * ie;
+                if (A.b >= 0) {  // u^m of a stored pair: its model rows into the slab
+                    const float* u = C.ckpt_field((size_t)A.b + 1, 1) +
+                                     ((size_t)p->nb * C.d.NY + p->nb) * C.d.NX;
+                    CU(cudaMemcpy2DAsync(slab, row, u, sizeof(float) * (size_t)C.d.NY * C.d.NX,
+                                         row, (size_t)p->nz, cudaMemcpyDeviceToDevice, C.s));
+                }
+                for (; m_next > m_img; m_next--) {
+                    if (m_next % ie == 0) return fail(RTM_ERR_STATE, "schedule skipped step %d", m_next);
+                    CHECK(back_step(m_next, nullptr));
+                }
+                CHECK(back_step(m_img, slab));
+                m_next = m_img - 1;
+                break;
+            }
+            default:
+                break;
+        }
+    }
+    for (; m_next >= 1; m_next--) {
+        if (m_next % ie == 0) return fail(RTM_ERR_STATE, "schedule skipped step %d", m_next);
+        CHECK(back_step(m_next, nullptr));
+    }
+    return RTM_OK;
+}
+
 // receiver propagation, imaging (grad = false) or gradient accumulation (grad = true)
 rtm_status run_backward(Ctx& C, const int32_t* rec, const float* rdata, float* src_adj,
                         bool grad) {
@@ -499,6 +588,8 @@ rtm_status run_backward(Ctx& C, const int32_t* rec, const float* rdata, float* s
             }
             CHECK(back_step(m, slab));
         }
+    } else if (p->storage == RTM_STORE_REVOLVE) {
+        CHECK(run_revolve(C, rec, back_step));
     } else if (p->storage == RTM_STORE_ALL) {
         for (int m = p->nt; m >= 1; m--) {
             float* snap = nullptr;
@@ -765,6 +856,27 @@ rtm_status rtm_backward_image_illum(const rtm_params* p, const float* d_c, const
     CU(launch_image_finalize(C.G, C.at(C.L.img), d_image, C.s));
     count_launch();
     return finish(C);
+}
+
+int64_t rtm_revolve_cost(int32_t nstates, int32_t slots) {
+    if (nstates < 0 || slots < 0) return -1;
+    return revolve_cost(nstates, slots);
+}
+
+int32_t rtm_revolve_schedule(int32_t nstates, int32_t slots, int32_t* h_actions,
+                             int32_t max_actions) {
+    if (nstates < 0 || slots < 0) return -1;
+    std::vector<RevolveAction> plan;
+    if (!revolve_schedule(nstates, slots, plan)) return -1;
+    const int32_t n = (int32_t)plan.size();
+    if (h_actions && n <= max_actions)
+        for (int32_t i = 0; i < n; i++) {
+            h_actions[4 * i] = plan[i].op;
+            h_actions[4 * i + 1] = plan[i].a;
+            h_actions[4 * i + 2] = plan[i].b;
+            h_actions[4 * i + 3] = plan[i].c;
+        }
+    return n;
 }
 
 rtm_status rtm_image_filter(const rtm_params* p, const float* d_image, const float* d_illum,
