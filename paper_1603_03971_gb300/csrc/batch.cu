@@ -138,12 +138,18 @@ __device__ void process_item(const BatchArgs& A, const BatchShot& S, const Batch
 #pragma unroll
         for (int i = 0; i < 4; i++) gxy.v[i] = S.gx[x + i] * gyv;
     }
-    F4 q[2 * R + 1];
+    // the z loop runs in groups of U planes: step t reads its centre as
+    // q[R + t] and prefetches the next head into q[2R + t + 1]; the queue
+    // moves by U once per group (2R / U register moves per plane)
+    constexpr int U = (R == 8) ? 4 : 1;
+    F4 q[2 * R + U + 1];
 #pragma unroll
     for (int i = 0; i < 2 * R + 1; i++) {
         const int zz = zb - R + i;
         q[i] = (rd && zz >= 0 && zz < S.NZ) ? ld_l2(cur + (size_t)zz * plane + col) : zero4();
     }
+#pragma unroll
+    for (int i = 2 * R + 1; i < 2 * R + U + 1; i++) q[i] = zero4();
     F4 hxv = hx_ok ? ld_l2(cur + (size_t)zb * plane + hx_col) : zero4();
     F4 hyv = hy_ok ? ld_l2(cur + (size_t)zb * plane + hy_col) : zero4();
     F4 up = rd ? ld_l2(prev + (size_t)zb * plane + col) : zero4();
@@ -152,9 +158,13 @@ __device__ void process_item(const BatchArgs& A, const BatchShot& S, const Batch
     const bool do_src = ph.kind != PH_BWD;
     const float w = do_src ? A.wavelet[ph.step] : 0.f;
 
-    for (int z = zb; z < ze; z++) {
+    for (int zg = zb; zg < ze; zg += U) {
+#pragma unroll
+    for (int t = 0; t < U; t++) {
+        const int z = zg + t;
+        if (z >= ze) break;  // the same for every thread of the block
         float(*Sm)[T::SW] = sm[(z - zb) & 1];
-        sts4(&Sm[R + ty][R + 4 * tx], q[R]);
+        sts4(&Sm[R + ty][R + 4 * tx], q[R + t]);
         if (hx_left || hx_right) sts4(&Sm[R + ty][hx_sc], hxv);
         if (hy_top || hy_bot) sts4(&Sm[hy_sr][R + 4 * tx], hyv);
         const int zn = z + 1;
@@ -181,10 +191,10 @@ __device__ void process_item(const BatchArgs& A, const BatchShot& S, const Batch
                 }
             }
 #pragma unroll
-            for (int i = 0; i < 4; i++) v[R + i] = q[R].v[i];
+            for (int i = 0; i < 4; i++) v[R + i] = q[R + t].v[i];
             F4 lap;
 #pragma unroll
-            for (int i = 0; i < 4; i++) lap.v[i] = A.a[0] * q[R].v[i];
+            for (int i = 0; i < 4; i++) lap.v[i] = A.a[0] * q[R + t].v[i];
 #pragma unroll
             for (int k = 1; k <= R; k++) {
                 const F4 ym_ = lds4(&Sm[R + ty - k][R + 4 * tx]);
@@ -193,7 +203,7 @@ __device__ void process_item(const BatchArgs& A, const BatchShot& S, const Batch
                 for (int i = 0; i < 4; i++) {
                     const float px = v[R + i - k] + v[R + i + k];
                     const float py = ym_.v[i] + yp_.v[i];
-                    const float pz = q[R - k].v[i] + q[R + k].v[i];
+                    const float pz = q[R + t - k].v[i] + q[R + t + k].v[i];
                     lap.v[i] = fmaf(A.a[k], (px + py) + pz, lap.v[i]);
                 }
             }
@@ -202,7 +212,7 @@ __device__ void process_item(const BatchArgs& A, const BatchShot& S, const Batch
 #pragma unroll
             for (int i = 0; i < 4; i++) {
                 const float g = gxy.v[i] * gzv;
-                out.v[i] = g * fmaf(cc.v[i], lap.v[i], 2.0f * q[R].v[i]) - (g * g) * up.v[i];
+                out.v[i] = g * fmaf(cc.v[i], lap.v[i], 2.0f * q[R + t].v[i]) - (g * g) * up.v[i];
             }
             // source injection: u^{n+1}[s] += c_s w^n / dx^3
             if (do_src && z == S.src_z && y == S.src_y && S.src_x >= x && S.src_x < x + 4)
@@ -222,7 +232,7 @@ __device__ void process_item(const BatchArgs& A, const BatchShot& S, const Batch
             st_plain4(prev + o, out);
             if (clear) st_plain4(clear + o, zero4());
             if (ck_a) {
-                st_plain4(ck_a + o, q[R]);
+                st_plain4(ck_a + o, q[R + t]);
                 st_plain4(ck_b + o, out);
             }
             const bool inm = xm && ym && z >= S.nb && z < S.nb + S.nz;
@@ -246,13 +256,14 @@ __device__ void process_item(const BatchArgs& A, const BatchShot& S, const Batch
                 }
             }
         }
-#pragma unroll
-        for (int i = 0; i < 2 * R; i++) q[i] = q[i + 1];
-        q[2 * R] = qn;
+        q[2 * R + t + 1] = qn;
         hxv = hxn;
         hyv = hyn;
         up = upn;
         cc = ccn;
+    }
+#pragma unroll
+        for (int i = 0; i <= 2 * R; i++) q[i] = q[i + U];
     }
 }
 

@@ -70,7 +70,7 @@ struct Emitter {
     const Plan& P;
     std::vector<RevolveAction>& out;
     std::vector<int> free_slots;
-    int cur = 0;  // state held by the working pair
+    int cur = -1;  // state held by the working pair (none known at the start)
 
     void restore(int slot, int a) {
         if (cur != a) {
@@ -124,7 +124,7 @@ bool revolve_schedule(int n, int s, std::vector<RevolveAction>& out) {
     out.clear();
     auto P = plan_for(n, s);
     if (!P) return false;
-    Emitter E{*P, out, {}, 0};
+    Emitter E{*P, out, {}, -1};
     for (int i = P->s - 1; i >= 0; i--) E.free_slots.push_back(i);
     E.run(0, n, P->s, -1);
     return true;

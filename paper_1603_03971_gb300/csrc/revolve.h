@@ -13,7 +13,8 @@
 // states with one slot fewer, deliver X_c from its slot and free it; then
 // the c - 1 earlier states from X_0 again), the recursion behind binomial
 // (revolve) checkpointing. Table and split points are computed once per
-// (n, s) by dynamic programming, O(n^2 s).
+// (n, s) by dynamic programming, O(n^2 s). The schedule assumes nothing
+// about the working pair at its start: its first action restores X_0.
 #pragma once
 
 #include <stdint.h>

@@ -66,7 +66,7 @@ def _simulate(n, s, actions):
     """Replays the actions: returns the forward steps taken; asserts that
     every state is delivered once, in order n..1, from where the action says
     it is, and that no more than s slots are ever in use."""
-    work, slots, steps, expect = 0, {}, 0, n
+    work, slots, steps, expect = None, {}, 0, n  # the working pair starts unknown
     for op, a, b, c in actions:
         if op == 0:  # restore
             if a < 0:
@@ -76,16 +76,16 @@ def _simulate(n, s, actions):
                 work = b
             assert work == b
         elif op == 1:  # advance
-            assert work == a and b > a
+            assert work is not None and work == a and b > a
             steps += b - a
             work = b
         elif op == 2:  # store
-            assert a not in slots and 0 <= a < s and work == b
+            assert a not in slots and 0 <= a < s and work is not None and work == b
             slots[a] = b
         elif op == 3:  # deliver
             assert a == expect
             if b < 0:
-                assert work == a
+                assert work is not None and work == a
             else:
                 assert slots.get(b) == a
             expect -= 1
