@@ -56,7 +56,7 @@ def parse():
                     help="oracle time steps per bench step of the reference arm")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-compression leg (384^3, 3000 steps)")
-    ap.add_argument("--learned-train-steps", type=int, default=4000)
+    ap.add_argument("--learned-train-steps", type=int, default=20000)
     ap.add_argument("--learned-models", type=int, default=64)
     ap.add_argument("--batch", action="store_true",
                     help="also run the batched-shots leg (32 apertures, radius 8)")

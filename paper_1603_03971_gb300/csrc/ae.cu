@@ -804,49 +804,77 @@ __global__ void k_loss(const float* __restrict__ y, Vol in, const float* inv_sig
 // patch-conv weight gradients (rank 8) and the bias gradients:
 //   dW1[c][d] += sum_v ga1[v][c] xq[2v + d],   dW4[d][i] += sum_v gy[2v + d] g1[v][i]
 //   db1 += sum ga1, db2 += sum glat, db3 += sum ga3
-// thread t of a block owns output t (256 = 32 x 8); blocks split the voxels
-__global__ void k_small_grads(Vol in, const float* inv_sigma, const bf16* __restrict__ ga1,
-                              const bf16* __restrict__ gy, const bf16* __restrict__ g1,
-                              const bf16* __restrict__ ga3, const bf16* __restrict__ glat,
-                              Dims3 h, Dims3 l, float* grad) {
-    const int t = threadIdx.x;  // 256 threads
+// a warp per voxel, lane = channel: lanes 0..7 load the voxel's 8 patch
+// inputs and lanes 8..15 its 8 output gradients, shared by shuffles; each
+// lane accumulates its row of the two outer products; the 8 warps of a block
+// are summed in shared memory and the block adds its sums with one atomic per
+// output
+__global__ void __launch_bounds__(256) k_small_grads(Vol in, const float* inv_sigma,
+                                                     const bf16* __restrict__ ga1,
+                                                     const bf16* __restrict__ gy,
+                                                     const bf16* __restrict__ g1,
+                                                     const bf16* __restrict__ ga3,
+                                                     const bf16* __restrict__ glat, Dims3 h,
+                                                     Dims3 l, float* grad) {
+    constexpr int kVals = 19;  // per lane: dW1 row (8), dW4 column (8), db1, db3, db2
+    __shared__ float red[8][kVals][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const long long nh = (long long)h.nx * h.ny * h.nz;
     const long long nl = (long long)l.nx * l.ny * l.nz;
-    const long long per = (nh + gridDim.x - 1) / gridDim.x;
-    const long long v0 = blockIdx.x * per, v1 = min(nh, v0 + per);
+    const long long gw = (long long)blockIdx.x * 8 + wid, nw = (long long)gridDim.x * 8;
     const float s = *inv_sigma;
     const int NX = 2 * h.nx, NY = 2 * h.ny;
-    const int c = t >> 3, d = t & 7;  // dW1 output (c, d)
-    const int dd = t >> 5, i = t & 31;  // dW4 output (d, i)
-    const int dz = d >> 2, dy = (d >> 1) & 1, dx = d & 1;
-    const int ez = dd >> 2, ey = (dd >> 1) & 1, ex = dd & 1;
-    float w1 = 0.f, w4 = 0.f, b1 = 0.f, b3 = 0.f;
-    for (long long v = v0; v < v1; v++) {
+    const int e = lane & 7, ez = e >> 2, ey = (e >> 1) & 1, ex = e & 1;
+    float w1[8], w4[8], b1 = 0.f, b3 = 0.f, b2 = 0.f;
+#pragma unroll
+    for (int d = 0; d < 8; d++) w1[d] = w4[d] = 0.f;
+    for (long long v = gw; v < nh; v += nw) {
         int x, y, z;
         decode3(v, h.nx, h.ny, x, y, z);
-        const float xq = __bfloat162float(__float2bfloat16_rn(
-            in.p[(long long)(2 * z + dz) * in.sz + (long long)(2 * y + dy) * in.sy + 2 * x + dx] * s));
-        const float ga = __bfloat162float(ga1[v * 32 + c]);
-        w1 += ga * xq;
-        const float g = __bfloat162float(gy[((long long)(2 * z + ez) * NY + (2 * y + ey)) * NX + 2 * x + ex]);
-        w4 += g * __bfloat162float(g1[v * 32 + i]);
-        if (t < 32) {
-            b1 += __bfloat162float(ga1[v * 32 + t]);
-            b3 += __bfloat162float(ga3[v * 32 + t]);
+        float mine = 0.f;
+        if (lane < 8)
+            mine = __bfloat162float(__float2bfloat16_rn(
+                in.p[(long long)(2 * z + ez) * in.sz + (long long)(2 * y + ey) * in.sy + 2 * x + ex] *
+                s));
+        else if (lane < 16)
+            mine = __bfloat162float(
+                gy[((long long)(2 * z + ez) * NY + (2 * y + ey)) * NX + 2 * x + ex]);
+        const float a = __bfloat162float(ga1[v * 32 + lane]);
+        const float gg = __bfloat162float(g1[v * 32 + lane]);
+        b1 += a;
+        b3 += __bfloat162float(ga3[v * 32 + lane]);
+#pragma unroll
+        for (int d = 0; d < 8; d++) {
+            w1[d] = fmaf(a, __shfl_sync(0xffffffffu, mine, d), w1[d]);
+            w4[d] = fmaf(__shfl_sync(0xffffffffu, mine, 8 + d), gg, w4[d]);
         }
     }
-    atomicAdd(&grad[kOW1 + c * 8 + d], w1);
-    atomicAdd(&grad[kOW4 + dd * 32 + i], w4);
-    if (t < 32) {
-        atomicAdd(&grad[kOB1 + t], b1);
-        atomicAdd(&grad[kOB3 + t], b3);
+    if (lane < 16)
+        for (long long v = gw; v < nl; v += nw) b2 += __bfloat162float(glat[v * 16 + lane]);
+#pragma unroll
+    for (int d = 0; d < 8; d++) {
+        red[wid][d][lane] = w1[d];
+        red[wid][8 + d][lane] = w4[d];
     }
-    if (t < 16) {
-        const long long per_l = (nl + gridDim.x - 1) / gridDim.x;
-        const long long u0 = blockIdx.x * per_l, u1 = min(nl, u0 + per_l);
-        float b2 = 0.f;
-        for (long long v = u0; v < u1; v++) b2 += __bfloat162float(glat[v * 16 + t]);
-        atomicAdd(&grad[kOB2 + t], b2);
+    red[wid][16][lane] = b1;
+    red[wid][17][lane] = b3;
+    red[wid][18][lane] = b2;
+    __syncthreads();
+    for (int k = threadIdx.x; k < kVals * 32; k += blockDim.x) {
+        const int val = k >> 5, ln = k & 31;
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; w++) t += red[w][val][ln];
+        if (val < 8)
+            atomicAdd(&grad[kOW1 + ln * 8 + val], t);
+        else if (val < 16)
+            atomicAdd(&grad[kOW4 + (val - 8) * 32 + ln], t);
+        else if (val == 16)
+            atomicAdd(&grad[kOB1 + ln], t);
+        else if (val == 17)
+            atomicAdd(&grad[kOB3 + ln], t);
+        else if (ln < 16)
+            atomicAdd(&grad[kOB2 + ln], t);
     }
 }
 
@@ -979,7 +1007,7 @@ cudaError_t ae_sample_grad(const float* P, const Vol& in, float scale, const AeT
         return e;
     E2dArgs d0{b.glat, l, b.h1, h, P, b.ga1};
     if ((e = run<OpE2d>(d0, dim3(tiles(nh)), status, s)) != cudaSuccess) return e;
-    long long sb = (nh + 4095) / 4096;
+    long long sb = (nh + 8 * 64 - 1) / (8 * 64);  // at least 64 voxels per warp
     if (sb < 1) sb = 1;
     if (sb > 152 * 4) sb = 152 * 4;
     k_small_grads<<<(unsigned)sb, 256, 0, s>>>(in, &sc->inv_sigma, b.ga1, b.gy, b.g1, b.ga3,
