@@ -38,9 +38,106 @@ struct TmaMaps {
     CUtensorMap u, prev, c, e1, e2;
 };
 
+// V consecutive x points per thread: 4 (16-byte vectors) at radius 4; 2 at
+// radius 8, where the 2r + 1 deep register queue of 4-point vectors would
+// hold a block to one per SM
+template <int R>
+__host__ __device__ constexpr int points_per_thread() {
+    return R == 8 ? 2 : 4;
+}
+
+template <int R, int V>
+struct TmaTile {
+    static constexpr int BX = 16;          // threads along x, V floats each
+    static constexpr int BY = 16;          // threads along y
+    static constexpr int TX = V * BX;      // floats
+    static constexpr int TY = BY;          // rows
+    static constexpr int SW = TX + 2 * R;  // shared row width (floats)
+    static constexpr int SH = TY + 2 * R;  // shared rows
+    static constexpr int HX = R / V;       // halo vectors per side per row
+    static_assert(R % 4 == 0 && R % V == 0, "radius must be a multiple of 4 and of V");
+    static_assert(TY >= 2 * R, "tile too short");
+};
+
+template <int V>
+struct Vec {
+    float v[V];
+};
+template <int V>
+__device__ __forceinline__ Vec<V> vzero() {
+    Vec<V> r;
+#pragma unroll
+    for (int i = 0; i < V; i++) r.v[i] = 0.f;
+    return r;
+}
+template <int V>
+__device__ __forceinline__ Vec<V> vlds(const float* p) {  // shared memory
+    Vec<V> r;
+    if constexpr (V == 4) {
+        const float4 t = *reinterpret_cast<const float4*>(p);
+        r.v[0] = t.x, r.v[1] = t.y, r.v[2] = t.z, r.v[3] = t.w;
+    } else {
+        const float2 t = *reinterpret_cast<const float2*>(p);
+        r.v[0] = t.x, r.v[1] = t.y;
+    }
+    return r;
+}
+template <int V>
+__device__ __forceinline__ Vec<V> vld_keep(const float* p) {  // read-only global, keep cached
+    Vec<V> r;
+    if constexpr (V == 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+        r.v[0] = t.x, r.v[1] = t.y, r.v[2] = t.z, r.v[3] = t.w;
+    } else {
+        const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+        r.v[0] = t.x, r.v[1] = t.y;
+    }
+    return r;
+}
+template <int V>
+__device__ __forceinline__ void vst_stream(float* p, const Vec<V>& a) {
+    if constexpr (V == 4)
+        __stcs(reinterpret_cast<float4*>(p), make_float4(a.v[0], a.v[1], a.v[2], a.v[3]));
+    else
+        __stcs(reinterpret_cast<float2*>(p), make_float2(a.v[0], a.v[1]));
+}
+
+// packed fp32 pairs (sm_100 family f32x2 arithmetic: IEEE single precision
+// per lane, two lanes per instruction)
+__device__ __forceinline__ uint64_t pk2(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(uint64_t r, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// the Laplacian on packed pairs of points: the same sums in the same order
+// as the scalar form, with half the floating-point instructions
+template <int R>
+__host__ __device__ constexpr bool packed_math() {
+    return R == 8;
+}
+
 template <int R, int NA>
 struct TmaCfg {
-    using T = Tile<R>;
+    using T = TmaTile<R, points_per_thread<R>()>;
     static constexpr int SU = R + kPrefetch + 1;
     static constexpr int SA = kPrefetch + 1;
     static constexpr int UPLANE = T::SH * T::SW;  // floats
@@ -90,13 +187,16 @@ __device__ __forceinline__ void tma3(float* dst, const CUtensorMap* map, int x, 
 // 98 KB) fit two
 template <int R, int MODE>
 constexpr int tma_min_blocks() {
-    return R != 4 ? 1 : ((MODE == MODE_BWD_IMAGE || MODE == MODE_BWD_GRAD) ? 2 : 3);
+    // radius 8 (two points per thread): 78-92 KB, two blocks
+    return R != 4 ? 2 : ((MODE == MODE_BWD_IMAGE || MODE == MODE_BWD_GRAD) ? 2 : 3);
 }
 
 template <int R, int MODE>
 __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
     k_stencil_tma(const __grid_constant__ StepArgs A, const __grid_constant__ TmaMaps M, int* status) {
-    using T = Tile<R>;
+    constexpr int V = points_per_thread<R>();
+    using T = TmaTile<R, V>;
+    using VT = Vec<V>;
     constexpr int NA = (MODE == MODE_BWD_IMAGE || MODE == MODE_BWD_GRAD) ? 4 : 2;
     using C = TmaCfg<R, NA>;
     extern __shared__ __align__(128) float dsm[];
@@ -108,13 +208,13 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * T::BX + tx;
     const int x0 = blockIdx.x * T::TX, y0 = blockIdx.y * T::TY;
-    const int x = x0 + 4 * tx, y = y0 + ty;
+    const int x = x0 + V * tx, y = y0 + ty;
     const int zb = blockIdx.z * A.zchunk;
     const int ze = min(A.NZ, zb + A.zchunk);
     const bool own = x < A.NX && y < A.NY;
     const size_t plane = (size_t)A.NX * (size_t)A.NY;
     const size_t col = (size_t)y * A.NX + x;
-    const bool xm = (x + 3 >= A.nb) && (x < A.nb + A.nx);
+    const bool xm = (x + V - 1 >= A.nb) && (x < A.nb + A.nx);
     const bool ym = (y >= A.nb) && (y < A.nb + A.ny);
     const size_t slab_col = (size_t)(y - A.nb) * A.NX + x;
     const size_t slab_plane = (size_t)A.ny * A.NX;
@@ -152,23 +252,24 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
         for (int p = zb; p < zb + kPrefetch && p < ze; p++) issue_a(p);
     }
 
-    F4 gxy = zero4();
+    VT gxy = vzero<V>();
     if (own) {
         const float gyv = A.gy[y];
 #pragma unroll
-        for (int i = 0; i < 4; i++) gxy.v[i] = A.gx[x + i] * gyv;
+        for (int i = 0; i < V; i++) gxy.v[i] = A.gx[x + i] * gyv;
     }
     // queue planes zb - R .. zb + R - 1 straight from global memory
-    F4 q[2 * R + 1];
+    VT q[2 * R + 1];
 #pragma unroll
     for (int i = 0; i < 2 * R; i++) {
         const int zz = zb - R + i;
-        q[i] = (own && zz >= 0 && zz < A.NZ) ? ld_keep(A.u_cur + (size_t)zz * plane + col) : zero4();
+        q[i] = (own && zz >= 0 && zz < A.NZ) ? vld_keep<V>(A.u_cur + (size_t)zz * plane + col)
+                                             : vzero<V>();
     }
-    q[2 * R] = zero4();
+    q[2 * R] = vzero<V>();
 
-    const int own_off = (R + ty) * T::SW + R + 4 * tx;  // this vector in a u^n plane
-    const int aux_off = ty * T::TX + 4 * tx;             // this vector in an aux plane
+    const int own_off = (R + ty) * T::SW + R + V * tx;  // this vector in a u^n plane
+    const int aux_off = ty * T::TX + V * tx;             // this vector in an aux plane
 
     for (int z = zb; z < ze; z++) {
         if (tid == 0 && !abort_flag) {
@@ -178,7 +279,7 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
         const int ph = z + R;  // queue head plane
         const int sh = (ph - zb) % C::SU;
         bool ok = bar_wait(&ubar[sh], (uint32_t)(((ph - zb) / C::SU) & 1), &abort_flag);
-        q[2 * R] = lds4(uring + sh * C::UPLANE + own_off);
+        q[2 * R] = vlds<V>(uring + sh * C::UPLANE + own_off);
         const int sc = (z - zb) % C::SU;
         ok = bar_wait(&ubar[sc], (uint32_t)(((z - zb) / C::SU) & 1), &abort_flag) && ok;
         const int sa = (z - zb) % C::SA;
@@ -187,64 +288,91 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
         const float* aux = aring + sa * NA * C::APLANE;
 
         if (own && ok) {
-            float v[4 + 2 * R];
+            float v[V + 2 * R];
 #pragma unroll
             for (int h = 0; h < T::HX; h++) {
-                const F4 l = lds4(S + (R + ty) * T::SW + 4 * tx + 4 * h);
-                const F4 r = lds4(S + (R + ty) * T::SW + R + 4 * tx + 4 + 4 * h);
+                const VT l = vlds<V>(S + (R + ty) * T::SW + V * tx + V * h);
+                const VT r = vlds<V>(S + (R + ty) * T::SW + R + V * tx + V + V * h);
 #pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    v[4 * h + i] = l.v[i];
-                    v[R + 4 + 4 * h + i] = r.v[i];
+                for (int i = 0; i < V; i++) {
+                    v[V * h + i] = l.v[i];
+                    v[R + V + V * h + i] = r.v[i];
                 }
             }
 #pragma unroll
-            for (int i = 0; i < 4; i++) v[R + i] = q[R].v[i];
-            F4 lap;
+            for (int i = 0; i < V; i++) v[R + i] = q[R].v[i];
+            VT lap;
+            if constexpr (packed_math<R>()) {
+                uint64_t L2[V / 2];
+                const uint64_t a0 = pk2(A.a[0], A.a[0]);
 #pragma unroll
-            for (int i = 0; i < 4; i++) lap.v[i] = A.a[0] * q[R].v[i];
+                for (int j = 0; j < V / 2; j++)
+                    L2[j] = mul2(a0, pk2(q[R].v[2 * j], q[R].v[2 * j + 1]));
 #pragma unroll
-            for (int k = 1; k <= R; k++) {
-                const F4 ym_ = lds4(S + (R + ty - k) * T::SW + R + 4 * tx);
-                const F4 yp_ = lds4(S + (R + ty + k) * T::SW + R + 4 * tx);
+                for (int k = 1; k <= R; k++) {
+                    const VT ym_ = vlds<V>(S + (R + ty - k) * T::SW + R + V * tx);
+                    const VT yp_ = vlds<V>(S + (R + ty + k) * T::SW + R + V * tx);
+                    const uint64_t ak = pk2(A.a[k], A.a[k]);
 #pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    const float px = v[R + i - k] + v[R + i + k];
-                    const float py = ym_.v[i] + yp_.v[i];
-                    const float pz = q[R - k].v[i] + q[R + k].v[i];
-                    lap.v[i] = fmaf(A.a[k], (px + py) + pz, lap.v[i]);
+                    for (int j = 0; j < V / 2; j++) {
+                        const int i = 2 * j;
+                        const uint64_t px = add2(pk2(v[R + i - k], v[R + i + 1 - k]),
+                                                 pk2(v[R + i + k], v[R + i + 1 + k]));
+                        const uint64_t py = add2(pk2(ym_.v[i], ym_.v[i + 1]),
+                                                 pk2(yp_.v[i], yp_.v[i + 1]));
+                        const uint64_t pz = add2(pk2(q[R - k].v[i], q[R - k].v[i + 1]),
+                                                 pk2(q[R + k].v[i], q[R + k].v[i + 1]));
+                        L2[j] = fma2(ak, add2(add2(px, py), pz), L2[j]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < V / 2; j++) upk2(L2[j], lap.v[2 * j], lap.v[2 * j + 1]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < V; i++) lap.v[i] = A.a[0] * q[R].v[i];
+#pragma unroll
+                for (int k = 1; k <= R; k++) {
+                    const VT ym_ = vlds<V>(S + (R + ty - k) * T::SW + R + V * tx);
+                    const VT yp_ = vlds<V>(S + (R + ty + k) * T::SW + R + V * tx);
+#pragma unroll
+                    for (int i = 0; i < V; i++) {
+                        const float px = v[R + i - k] + v[R + i + k];
+                        const float py = ym_.v[i] + yp_.v[i];
+                        const float pz = q[R - k].v[i] + q[R + k].v[i];
+                        lap.v[i] = fmaf(A.a[k], (px + py) + pz, lap.v[i]);
+                    }
                 }
             }
-            const F4 up = lds4(aux + aux_off);
-            const F4 cc = lds4(aux + C::APLANE + aux_off);
+            const VT up = vlds<V>(aux + aux_off);
+            const VT cc = vlds<V>(aux + C::APLANE + aux_off);
             const float gzv = A.gz[z];
-            F4 out;
+            VT out;
 #pragma unroll
-            for (int i = 0; i < 4; i++) {
+            for (int i = 0; i < V; i++) {
                 const float g = gxy.v[i] * gzv;
                 out.v[i] = g * fmaf(cc.v[i], lap.v[i], 2.0f * q[R].v[i]) - (g * g) * up.v[i];
             }
             const size_t o = (size_t)z * plane + col;
-            st_stream(A.u_prev + o, out);
+            vst_stream<V>(A.u_prev + o, out);
             if constexpr (MODE == MODE_FWD_SNAP) {
                 if (xm && ym && z >= A.nb && z < A.nb + A.nz)
-                    st_stream(A.snap + (size_t)(z - A.nb) * slab_plane + slab_col, out);
+                    vst_stream<V>(A.snap + (size_t)(z - A.nb) * slab_plane + slab_col, out);
             } else if constexpr (MODE == MODE_BWD_IMAGE) {
                 if (xm && ym && z >= A.nb && z < A.nb + A.nz) {
-                    const F4 sv = lds4(aux + 2 * C::APLANE + aux_off);
-                    F4 acc = lds4(aux + 3 * C::APLANE + aux_off);
+                    const VT sv = vlds<V>(aux + 2 * C::APLANE + aux_off);
+                    VT acc = vlds<V>(aux + 3 * C::APLANE + aux_off);
 #pragma unroll
-                    for (int i = 0; i < 4; i++) acc.v[i] = fmaf(sv.v[i], out.v[i], acc.v[i]);
-                    st_stream(A.acc + (size_t)(z - A.nb) * slab_plane + slab_col, acc);
+                    for (int i = 0; i < V; i++) acc.v[i] = fmaf(sv.v[i], out.v[i], acc.v[i]);
+                    vst_stream<V>(A.acc + (size_t)(z - A.nb) * slab_plane + slab_col, acc);
                 }
             } else if constexpr (MODE == MODE_FWD_LU) {
-                st_stream(A.snap + o, lap);
+                vst_stream<V>(A.snap + o, lap);
             } else if constexpr (MODE == MODE_BWD_GRAD) {
-                const F4 sv = lds4(aux + 2 * C::APLANE + aux_off);
-                F4 acc = lds4(aux + 3 * C::APLANE + aux_off);
+                const VT sv = vlds<V>(aux + 2 * C::APLANE + aux_off);
+                VT acc = vlds<V>(aux + 3 * C::APLANE + aux_off);
 #pragma unroll
-                for (int i = 0; i < 4; i++) acc.v[i] = fmaf(out.v[i], sv.v[i], acc.v[i]);
-                st_stream(A.acc + o, acc);
+                for (int i = 0; i < V; i++) acc.v[i] = fmaf(out.v[i], sv.v[i], acc.v[i]);
+                vst_stream<V>(A.acc + o, acc);
             }
         }
         __syncthreads();  // every thread is done with planes z (centre, aux): slots reusable
@@ -277,7 +405,7 @@ cudaError_t make_map(CUtensorMap* m, const float* base, int nx, int ny, int nz, 
 
 template <int R, int MODE>
 cudaError_t launch_tma_t(const StepArgs& a, int* status, cudaStream_t s) {
-    using T = Tile<R>;
+    using T = TmaTile<R, points_per_thread<R>()>;
     constexpr int NA = (MODE == MODE_BWD_IMAGE || MODE == MODE_BWD_GRAD) ? 4 : 2;
     constexpr int smem = TmaCfg<R, NA>::SMEM;
     static bool attr = false;
