@@ -50,6 +50,8 @@ def parse():
                     help="override the model edge (profiling cases; the line is then not the "
                          "headline workload)")
     ap.add_argument("--ckpt-every", type=int, default=0, help="override the checkpoint interval")
+    ap.add_argument("--radius", type=int, default=0, choices=(0, 4, 8),
+                    help="override the stencil radius (profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-steps", type=int, default=2,
@@ -90,6 +92,8 @@ def workload(args):
         w = w.scaled(nx=n, ny=n, nz=n, src=(n // 2, n // 2, w.src[2]), name=w.name + "@%d" % n)
     if args.ckpt_every:
         w = w.scaled(ckpt_every=args.ckpt_every)
+    if args.radius:
+        w = w.scaled(radius=args.radius)
     return w
 
 
@@ -545,8 +549,9 @@ def run_ours(args):
     achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else None
     shares = {k: v["ms"] for k, v in st["stencil"].items() if v["launches"]}
     roofline = {
-        "kernel": ("k_stencil_tma<4, MODE_BWD_IMAGE>" if args.variant != 1 else
-                   "k_stencil<4, MODE_BWD_IMAGE>") + " (backward step + fused zero-lag imaging)",
+        "kernel": ("k_stencil_tma<%d, MODE_BWD_IMAGE>" if args.variant != 1 else
+                   "k_stencil<%d, MODE_BWD_IMAGE>") % w.radius
+                  + " (backward step + fused zero-lag imaging)",
         "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
         "frac": (achieved / hbm) if achieved else None, "peak_kind": peak_kind,
         "traffic": profiled_traffic(), "algorithmic_bytes_per_launch": per_launch_bytes,

@@ -88,7 +88,11 @@ typedef struct {
                                RTM_STORE_REVOLVE: binomial checkpointing in a
                                fixed number of slots (imaging only) */
     int32_t ckpt_every;     /* steps per checkpoint segment (RTM_STORE_CKPT);
-                               number of checkpoint slots (RTM_STORE_REVOLVE) */
+                               number of checkpoint slots (RTM_STORE_REVOLVE);
+                               exact window (RTM_STORE_LEARNED): the imaging
+                               snapshots of steps 1..ckpt_every are recomputed
+                               from the zero initial state in the backward
+                               call instead of being coded (0: none) */
     int32_t image_every;    /* image at steps m with m % image_every == 0 (>= 1) */
     int32_t want_grad;      /* 1: prepare the workspace for rtm_grad instead of imaging */
 } rtm_params;

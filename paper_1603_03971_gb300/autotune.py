@@ -74,10 +74,12 @@ def _time_forward(p, c, rec, ws, steps: int) -> float:
 
 
 def tune_stencil(radius: int, padded_shape: Tuple[int, int, int], steps: int = 12,
-                 cache_path: str = CACHE, force: bool = False) -> dict:
-    """Best z-slab height for the single-shot stencil on a padded grid
-    (NZ, NY, NX), timed on a constant-velocity model."""
-    from . import alloc_workspace, make_params, model_prep, set_tuning
+                 cache_path: str = CACHE, force: bool = False,
+                 variants: Tuple[int, ...] = (1, 2)) -> dict:
+    """Best plane-load variant (1 vector loads, 2 TMA) and z-slab height for
+    the single-shot stencil on a padded grid (NZ, NY, NX), timed on a
+    constant-velocity model; trials are keyed "variant/zchunk"."""
+    from . import RtmError, alloc_workspace, make_params, model_prep, set_tuning
 
     key = _key("stencil", radius, padded_shape)
     with _lock:
@@ -94,14 +96,18 @@ def tune_stencil(radius: int, padded_shape: Tuple[int, int, int], steps: int = 1
     rec = torch.zeros((1, 3), dtype=torch.int32, device="cuda")
     results = {}
     try:
-        for zc in candidates(NZ, radius):
-            set_tuning(radius, zc, 0)
-            results[zc] = _time_forward(p, c, rec, ws, steps)
+        for variant in variants:
+            for zc in candidates(NZ, radius):
+                try:
+                    set_tuning(radius, zc, variant)
+                    results[(variant, zc)] = _time_forward(p, c, rec, ws, steps)
+                except RtmError:
+                    continue  # a variant this driver cannot run
     finally:
         set_tuning(radius, 0, 0)
     best = min(results, key=results.get)
-    choice = {"zchunk": int(best), "variant": 0, "ms_per_step": results[best],
-              "trials": {str(k): v for k, v in results.items()}}
+    choice = {"zchunk": int(best[1]), "variant": int(best[0]), "ms_per_step": results[best],
+              "trials": {"%d/%d" % k: v for k, v in results.items()}}
     with _lock:
         cache = load_cache(cache_path)
         cache[key] = choice

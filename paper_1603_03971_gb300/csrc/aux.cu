@@ -150,11 +150,28 @@ __global__ void k_image_finalize(Geometry G, const float* __restrict__ slab,
 }
 
 // source illumination: illum[z][y][x] += u^2 of the model columns of a
-// snapshot slab [nz][ny][NX]
+// snapshot slab [nz][ny][NX]; 16-byte vectors along x when both rows allow
 __global__ void k_illum_add(Geometry G, const float* __restrict__ slab,
-                            float* __restrict__ illum) {
-    const long long n = (long long)G.nx * G.ny * G.nz;
+                            float* __restrict__ illum, int vec) {
     const long long stride = (long long)gridDim.x * blockDim.x;
+    if (vec) {
+        const int nx4 = G.nx >> 2;
+        const long long n4 = (long long)nx4 * G.ny * G.nz;
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+            const long long zy = i / nx4;
+            const int x4 = (int)(i - zy * nx4);
+            const float4 u = __ldcs(reinterpret_cast<const float4*>(slab + zy * G.NX + G.nb) + x4);
+            float4* d = reinterpret_cast<float4*>(illum + zy * G.nx) + x4;
+            float4 a = *d;
+            a.x = fmaf(u.x, u.x, a.x);
+            a.y = fmaf(u.y, u.y, a.y);
+            a.z = fmaf(u.z, u.z, a.z);
+            a.w = fmaf(u.w, u.w, a.w);
+            *d = a;
+        }
+        return;
+    }
+    const long long n = (long long)G.nx * G.ny * G.nz;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const long long zy = i / G.nx;
         const int x = (int)(i % G.nx);
@@ -319,7 +336,12 @@ cudaError_t launch_image_finalize(const Geometry& G, const float* slab, float* i
 cudaError_t launch_illum_add(const Geometry& G, const float* slab, float* illum,
                              cudaStream_t s) {
     const long long n = (long long)G.nx * G.ny * G.nz;
-    k_illum_add<<<grid_for(n, 256), 256, 0, s>>>(G, slab, illum);
+    // slab rows start 16-byte aligned (NX % 4 == 0); the model columns do
+    // when nb % 4 == 0, the illumination rows when nx % 4 == 0
+    const int vec = (G.nb % 4 == 0) && (G.nx % 4 == 0) &&
+                    (reinterpret_cast<uintptr_t>(illum) % 16 == 0) &&
+                    (reinterpret_cast<uintptr_t>(slab) % 16 == 0);
+    k_illum_add<<<grid_for(vec ? n / 4 : n, 256), 256, 0, s>>>(G, slab, illum, vec);
     return cudaGetLastError();
 }
 

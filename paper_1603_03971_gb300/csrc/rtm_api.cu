@@ -188,7 +188,10 @@ Layout layout_of(const rtm_params* p) {
         L.scales = take(sizeof(float) * (nlat ? nlat : 1));
         L.ae_h = take((size_t)(p->nx / 2) * (p->ny / 2) * (p->nz / 2) * 32 * 2);
         L.ae_scalars = take(256);
-        L.nsnap = 1;  // one snapshot slab, encoded or decoded in place
+        // one decode slab; an exact window of ckpt_every steps needs one slab
+        // per imaging step in it
+        const size_t nwin = (size_t)(p->ckpt_every / p->image_every);
+        L.nsnap = nwin > 1 ? nwin : 1;
     } else if (p->storage == RTM_STORE_ALL) {
         L.nsnap = p->want_grad ? (size_t)p->nt : (size_t)(p->nt / p->image_every);
     } else if (p->storage == RTM_STORE_REVOLVE) {
@@ -246,6 +249,8 @@ rtm_status validate(const rtm_params* p) {
                         p->nt / p->image_every, p->ckpt_every);
     }
     if (p->storage == RTM_STORE_LEARNED) {
+        if (p->ckpt_every < 0 || p->ckpt_every > p->nt)
+            return fail(RTM_ERR_INVALID, "exact window %d outside [0, nt]", p->ckpt_every);
         if (p->nx % 4 || p->ny % 4 || p->nz % 4)
             return fail(RTM_ERR_INVALID, "learned storage needs model sides that are multiples of 4");
         if (p->want_grad)
@@ -446,7 +451,7 @@ rtm_status run_forward(Ctx& C, const int32_t* rec, float* data, float* u_last) {
             }
         }
         CHECK(stencil(C, mode, cur, prev, snap, nullptr));
-        if (p->storage == RTM_STORE_LEARNED && (n + 1) % ie == 0) {
+        if (p->storage == RTM_STORE_LEARNED && (n + 1) % ie == 0 && n + 1 > p->ckpt_every) {
             // the encoder reads u^{n+1} (now in prev) in place: no snapshot copy
             const size_t k = (size_t)((n + 1) / ie - 1);
             CU(ae_encode(C.ae, C.field_view(prev), reinterpret_cast<ae::bf16*>(C.at(C.L.ae_h)),
@@ -576,10 +581,11 @@ rtm_status run_backward(Ctx& C, const int32_t* rec, const float* rdata, float* s
     };
 
     if (p->storage == RTM_STORE_LEARNED) {
+        const int W = p->ckpt_every;  // exact window: steps 1..W recomputed, not coded
         float* slab = C.snap_slot(0);
         // columns outside the model stay finite (the decoder writes model columns)
         CU(cudaMemsetAsync(slab, 0, sizeof(float) * C.d.slab, C.s));
-        for (int m = p->nt; m >= 1; m--) {
+        for (int m = p->nt; m > W; m--) {
             if (m % ie == 0) {
                 const size_t k = (size_t)(m / ie - 1);
                 CU(ae_decode(C.ae, C.latent_slot(k), C.at(C.L.scales) + k, C.model_view(slab),
@@ -587,6 +593,23 @@ rtm_status run_backward(Ctx& C, const int32_t* rec, const float* rdata, float* s
                 count_launch(1);
             }
             CHECK(back_step(m, slab));
+        }
+        if (W > 0) {  // checkpoint-recompute fallback from the zero initial state
+            float* rp = C.at(C.L.f[0]);
+            float* rc = C.at(C.L.f[1]);
+            CU(cudaMemsetAsync(rp, 0, fb, C.s));
+            CU(cudaMemsetAsync(rc, 0, fb, C.s));
+            for (int n = 0; n < W; n++) {
+                CHECK(fwd_aux(C, rc, rp, rec, nullptr, C.wav() + n));
+                const bool snap = (n + 1) % ie == 0;
+                CHECK(stencil(C, snap ? MODE_FWD_SNAP : MODE_FWD, rc, rp,
+                              snap ? C.snap_slot((size_t)((n + 1) / ie - 1)) : nullptr, nullptr));
+                float* t = rp;
+                rp = rc;
+                rc = t;
+            }
+            for (int m = W; m >= 1; m--)
+                CHECK(back_step(m, m % ie == 0 ? C.snap_slot((size_t)(m / ie - 1)) : nullptr));
         }
     } else if (p->storage == RTM_STORE_REVOLVE) {
         CHECK(run_revolve(C, rec, back_step));

@@ -31,8 +31,9 @@ def test_cache_round_trip(tmp_path):
 def test_tune_stencil_picks_the_fastest_and_caches(tmp_path):
     path = str(tmp_path / "tune.json")
     choice = autotune.tune_stencil(4, (104, 104, 104), steps=6, cache_path=path)
-    trials = {int(k): v for k, v in choice["trials"].items()}
-    assert choice["zchunk"] == min(trials, key=trials.get)
+    trials = {tuple(int(x) for x in k.split("/")): v for k, v in choice["trials"].items()}
+    assert {v for v, _ in trials} == {1, 2}  # both plane-load variants timed
+    assert (choice["variant"], choice["zchunk"]) == min(trials, key=trials.get)
     cached = json.load(open(path))
     assert any(v["zchunk"] == choice["zchunk"] for v in cached.values())
     # the second call is served from the cache

@@ -27,7 +27,8 @@ def _illum_run(g, d_obs, ae_params=None):
 
 
 @pytest.mark.parametrize("r,storage,ck,ie,shape", [
-    (4, "all", 0, 1, SMALL), (4, "ckpt", 9, 2, SMALL), (8, "ckpt", 16, 3, RAGGED)])
+    (4, "all", 0, 1, SMALL), (4, "ckpt", 9, 2, SMALL), (8, "ckpt", 16, 3, RAGGED),
+    (4, "ckpt", 7, 1, dict(nx=32, ny=24, nz=20, nb=8))])  # last: 16-byte vector path
 def test_illumination_matches_oracle(r, storage, ck, ie, shape):
     from oracle import imaging
 
