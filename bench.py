@@ -60,6 +60,9 @@ def parse():
                     help="skip the learned-compression leg (384^3, 3000 steps)")
     ap.add_argument("--learned-train-steps", type=int, default=20000)
     ap.add_argument("--learned-models", type=int, default=64)
+    ap.add_argument("--learned-window", type=int, default=200,
+                    help="exact window: the first steps whose snapshots are recomputed from the "
+                         "zero state instead of coded (checkpoint-recompute fallback)")
     ap.add_argument("--batch", action="store_true",
                     help="also run the batched-shots leg (32 apertures, radius 8)")
     ap.add_argument("--batch-nt", type=int, default=1500)
@@ -320,8 +323,9 @@ def learned_leg(args, dev):
     e1.record()
     torch.cuda.synchronize()
     t_ckpt = e0.elapsed_time(e1) / 1e3
+    ws_ckpt_gb = ws.numel() / 1e9
     del ws
-    pl = rtm.params_for(w, storage="learned")
+    pl = rtm.params_for(w, storage="learned", ckpt_every=args.learned_window)
     wl = rtm.alloc_workspace(pl, dev)
     img_l = torch.zeros_like(img_c)
     rtm.shot_learned(pl, c, rec, dobs, P, wl, img_l)  # warm-up
@@ -344,6 +348,10 @@ def learned_leg(args, dev):
                     "velocity, imaging every 4 steps (750 snapshots); observed data: scattered "
                     "field of three thin beds (+-8 %) at depths 96/192/288",
         "shot_s_checkpoint": t_ckpt, "checkpoint_every": 50,
+        "workspace_gb_checkpoint": ws_ckpt_gb, "workspace_gb_learned": wl.numel() / 1e9,
+        "exact_window_steps": args.learned_window,
+        "coded_snapshots": (w.nt - args.learned_window) // w.image_every,
+        "window_snapshots": args.learned_window // w.image_every,
         "shot_s_learned": t_learned, "speedup_vs_checkpoint": t_ckpt / t_learned,
         "image_rel_l2_vs_checkpoint": err, "target_rel_l2": 1e-2,
         "image_rel_l2_below_z16": err_deep,

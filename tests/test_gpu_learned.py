@@ -23,13 +23,14 @@ pytestmark = pytest.mark.gpu
 CODEC_TOL = 2e-3
 
 
-def _learned_image(case, g, P, d_obs_np):
+def _learned_image(case, g, P, d_obs_np, window=0):
     import torch
 
     import paper_1603_03971_gb300 as rtm
 
     pl = case.params()
     pl.storage = 2  # RTM_STORE_LEARNED
+    pl.ckpt_every = window  # exact window: steps 1..window recomputed, not coded
     wl = rtm.alloc_workspace(pl)
     dobs = torch.from_numpy(np.ascontiguousarray(d_obs_np, dtype=np.float32)).cuda()
     img = torch.zeros((case.nz, case.ny, case.nx), device="cuda")
@@ -38,7 +39,10 @@ def _learned_image(case, g, P, d_obs_np):
     return img.cpu().numpy().astype(np.float64)
 
 
-def test_learned_shot_matches_the_oracle_chain():
+@pytest.mark.parametrize("window", [0, 13])
+def test_learned_shot_matches_the_oracle_chain(window):
+    """With an exact window W the snapshots of steps 1..W are the exact ones
+    (recomputed), the later ones coded."""
     import torch
 
     from helpers import GpuRun
@@ -49,18 +53,36 @@ def test_learned_shot_matches_the_oracle_chain():
     P = rtm_inputs.ae_flat(rtm_inputs.ae_init_params(2)).astype(np.float32)
     g = GpuRun(case)
     d_obs = case.d_obs(g.nrec)
-    img = _learned_image(case, g, torch.from_numpy(P).cuda(), d_obs)
+    img = _learned_image(case, g, torch.from_numpy(P).cuda(), d_obs, window)
     # oracle: snapshots, codec and imaging, all on the CPU
     prob = case.oracle_problem()
     fw = prob.forward(keep_u=True)
     params = oae.unflatten(P.astype(np.float64))
     su = np.zeros_like(fw["u"])
     for m in range(ie, case.nt + 1, ie):
+        if m <= window:
+            su[m - 1] = fw["u"][m - 1]
+            continue
         lat, sc = oae.encode(params, fw["u"][m - 1].astype(np.float32).astype(np.float64))
         su[m - 1] = oae.decode(params, lat, sc)
     ref = prob.grid.adjoint(prob.w, prob.src, prob.rec, d_obs, snap_u=su,
                             image_every=ie)["image"]
     assert rel_l2(img, ref) <= CODEC_TOL
+
+
+def test_exact_window_over_the_whole_run_is_the_store_all_image():
+    import torch
+
+    from helpers import GpuRun
+
+    case = Case(nx=32, ny=28, nz=24, nb=8, r=4, nt=40, image_every=4)
+    P = torch.from_numpy(rtm_inputs.ae_flat(rtm_inputs.ae_init_params(2)).astype(np.float32)).cuda()
+    g = GpuRun(case)
+    d_obs = case.d_obs(g.nrec)
+    img = _learned_image(case, g, P, d_obs, window=case.nt)
+    g.forward()
+    ref = g.backward_image(d_obs)[0].cpu().numpy().astype(np.float64)
+    np.testing.assert_array_equal(img, ref)
 
 
 def test_trained_codec_beats_the_untrained_network():
