@@ -128,10 +128,17 @@ __device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
     return r;
 }
 
-// the Laplacian on packed pairs of points: the same sums in the same order
-// as the scalar form, with half the floating-point instructions
+// the Laplacian on packed pairs of points, with half the floating-point
+// instructions. Radius 4 keeps the scalar form's order of sums (two point
+// pairs per thread already give two independent chains); radius 8 (one pair
+// per thread, eight offsets) sums even and odd offsets separately and then
+// adds, halving the dependent chain
 template <int R>
 __host__ __device__ constexpr bool packed_math() {
+    return true;
+}
+template <int R>
+__host__ __device__ constexpr bool split_chains() {
     return R == 8;
 }
 
@@ -303,11 +310,13 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
             for (int i = 0; i < V; i++) v[R + i] = q[R].v[i];
             VT lap;
             if constexpr (packed_math<R>()) {
-                uint64_t L2[V / 2];
+                uint64_t L2[V / 2], L2o[V / 2];
                 const uint64_t a0 = pk2(A.a[0], A.a[0]);
 #pragma unroll
-                for (int j = 0; j < V / 2; j++)
+                for (int j = 0; j < V / 2; j++) {
                     L2[j] = mul2(a0, pk2(q[R].v[2 * j], q[R].v[2 * j + 1]));
+                    L2o[j] = 0;  // the bit pattern of two +0.0f
+                }
 #pragma unroll
                 for (int k = 1; k <= R; k++) {
                     const VT ym_ = vlds<V>(S + (R + ty - k) * T::SW + R + V * tx);
@@ -322,11 +331,19 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
                                                  pk2(yp_.v[i], yp_.v[i + 1]));
                         const uint64_t pz = add2(pk2(q[R - k].v[i], q[R - k].v[i + 1]),
                                                  pk2(q[R + k].v[i], q[R + k].v[i + 1]));
-                        L2[j] = fma2(ak, add2(add2(px, py), pz), L2[j]);
+                        if (split_chains<R>() && (k & 1))
+                            L2o[j] = fma2(ak, add2(add2(px, py), pz), L2o[j]);
+                        else
+                            L2[j] = fma2(ak, add2(add2(px, py), pz), L2[j]);
                     }
                 }
 #pragma unroll
-                for (int j = 0; j < V / 2; j++) upk2(L2[j], lap.v[2 * j], lap.v[2 * j + 1]);
+                for (int j = 0; j < V / 2; j++) {
+                    if constexpr (split_chains<R>())
+                        upk2(add2(L2[j], L2o[j]), lap.v[2 * j], lap.v[2 * j + 1]);
+                    else
+                        upk2(L2[j], lap.v[2 * j], lap.v[2 * j + 1]);
+                }
             } else {
 #pragma unroll
                 for (int i = 0; i < V; i++) lap.v[i] = A.a[0] * q[R].v[i];

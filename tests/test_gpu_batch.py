@@ -132,3 +132,56 @@ def test_batch_wait_timeout_is_reported_not_hung():
     img, _ = _run(p, vel, dobs)
     ref, _ = _oracle(p, vel, dobs)
     assert rel_l2(img, ref) <= TOL
+
+
+def test_batch_at_full_size_matches_single_shots():
+    """The batched-shots workload at its full size (1024 x 1024 x 512 layered
+    / salt model, radius 8, apertures from 128 x 128 x 256 upward): four of
+    its seeded apertures, 60 steps, checkpoints every 10. The oracle cannot
+    run these sizes; the single-shot path, checked against the oracle on
+    every shape class, is the reference: the batched image equals the sum of
+    the single-shot images of the same apertures and data within the
+    wavefield tolerance (the two paths form their FP32 sums in different
+    orders)."""
+    import torch
+
+    import paper_1603_03971_gb300 as rtm
+    from paper_1603_03971_gb300 import batch
+
+    cfg = rtm_inputs.BATCH_WORKLOAD
+    nz, ny, nx = cfg["model_shape"]
+    nt, nb, r = 60, cfg["nb"], cfg["radius"]
+    vel_np = rtm_inputs.layered_salt_velocity(nx, ny, nz, seed=cfg["seed"])
+    vel = torch.from_numpy(vel_np).cuda()
+    origin, size = rtm_inputs.batch_apertures(cfg["nshots"], (nz, ny, nx), seed=cfg["seed"])
+    pick = [0, 1, 2, 3]
+    aps = [batch.Aperture(int(origin[i][0]), int(origin[i][1]), int(origin[i][2]), int(size[i][0]),
+                          int(size[i][1]), int(size[i][2]), int(size[i][0]) // 2,
+                          int(size[i][1]) // 2, 4, 2) for i in pick]
+    dt = rtm_inputs.courant_dt(cfg["dx"], cfg["vmax"])
+    p = rtm.make_params(nx, ny, nz, nb, r, nt, cfg["dx"], dt, cfg["f0"], 1.0 / cfg["f0"],
+                        (0, 0, 0), 0, storage="ckpt", ckpt_every=10)
+    dobs = [rtm_inputs.standard_normal((nt, a.ny, a.nx), seed=90 + i).astype(np.float32) * 1e-3
+            for i, a in enumerate(aps)]
+    d = torch.from_numpy(np.concatenate([x.ravel() for x in dobs])).cuda()
+    img = torch.zeros((nz, ny, nx), device="cuda")
+    ws = batch.alloc_workspace(p, aps)
+    batch.run(p, aps, vel, d, img, ws)
+    rtm.check(ws)
+    del ws
+    ref = torch.zeros_like(img)
+    for a, dd in zip(aps, dobs):
+        q = rtm.make_params(a.nx, a.ny, a.nz, nb, r, nt, cfg["dx"], dt, cfg["f0"],
+                            1.0 / cfg["f0"], (a.src_x, a.src_y, a.src_z), a.nx * a.ny,
+                            storage="ckpt", ckpt_every=10)
+        w = rtm.alloc_workspace(q)
+        v = vel[a.oz:a.oz + a.nz, a.oy:a.oy + a.ny, a.ox:a.ox + a.nx].contiguous()
+        c = rtm.model_prep(q, v, w)
+        rec = torch.from_numpy(rtm_inputs.surface_receivers(a.nx, a.ny, a.rec_z)).cuda()
+        im = torch.zeros((a.nz, a.ny, a.nx), device="cuda")
+        rtm.shot(q, c, rec, torch.from_numpy(dd.reshape(nt, -1)).cuda(), w, im)
+        rtm.check(w)
+        ref[a.oz:a.oz + a.nz, a.oy:a.oy + a.ny, a.ox:a.ox + a.nx] += im
+        del w
+    assert float(ref.abs().max()) > 0
+    assert rel_l2(img.cpu().numpy(), ref.cpu().numpy()) <= TOL
