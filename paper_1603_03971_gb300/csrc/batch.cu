@@ -20,6 +20,7 @@
 // before it increments the shot's counter.
 
 #include "batch_internal.h"
+#include "packed_f32x2.cuh"
 #include "stencil_common.cuh"
 
 namespace rtm {
@@ -192,20 +193,36 @@ __device__ void process_item(const BatchArgs& A, const BatchShot& S, const Batch
             }
 #pragma unroll
             for (int i = 0; i < 4; i++) v[R + i] = q[R + t].v[i];
+            // the Laplacian on packed point pairs (f32x2), in the scalar
+            // form's order of sums
             F4 lap;
+            {
+                namespace P2 = f32x2;
+                uint64_t L2[2];
+                const uint64_t a0 = P2::pack(A.a[0], A.a[0]);
 #pragma unroll
-            for (int i = 0; i < 4; i++) lap.v[i] = A.a[0] * q[R + t].v[i];
+                for (int j = 0; j < 2; j++)
+                    L2[j] = P2::mul(a0, P2::pack(q[R + t].v[2 * j], q[R + t].v[2 * j + 1]));
 #pragma unroll
-            for (int k = 1; k <= R; k++) {
-                const F4 ym_ = lds4(&Sm[R + ty - k][R + 4 * tx]);
-                const F4 yp_ = lds4(&Sm[R + ty + k][R + 4 * tx]);
+                for (int k = 1; k <= R; k++) {
+                    const F4 ym_ = lds4(&Sm[R + ty - k][R + 4 * tx]);
+                    const F4 yp_ = lds4(&Sm[R + ty + k][R + 4 * tx]);
+                    const uint64_t ak = P2::pack(A.a[k], A.a[k]);
 #pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    const float px = v[R + i - k] + v[R + i + k];
-                    const float py = ym_.v[i] + yp_.v[i];
-                    const float pz = q[R + t - k].v[i] + q[R + t + k].v[i];
-                    lap.v[i] = fmaf(A.a[k], (px + py) + pz, lap.v[i]);
+                    for (int j = 0; j < 2; j++) {
+                        const int i = 2 * j;
+                        const uint64_t px = P2::add(P2::pack(v[R + i - k], v[R + i + 1 - k]),
+                                                    P2::pack(v[R + i + k], v[R + i + 1 + k]));
+                        const uint64_t py = P2::add(P2::pack(ym_.v[i], ym_.v[i + 1]),
+                                                    P2::pack(yp_.v[i], yp_.v[i + 1]));
+                        const uint64_t pz =
+                            P2::add(P2::pack(q[R + t - k].v[i], q[R + t - k].v[i + 1]),
+                                    P2::pack(q[R + t + k].v[i], q[R + t + k].v[i + 1]));
+                        L2[j] = P2::fma(ak, P2::add(P2::add(px, py), pz), L2[j]);
+                    }
                 }
+#pragma unroll
+                for (int j = 0; j < 2; j++) P2::unpack(L2[j], lap.v[2 * j], lap.v[2 * j + 1]);
             }
             const float gzv = S.gz[z];
             F4 out;
