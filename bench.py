@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--learned-window", type=int, default=200,
                     help="exact window: the first steps whose snapshots are recomputed from the "
                          "zero state instead of coded (checkpoint-recompute fallback)")
+    ap.add_argument("--no-boundary", action="store_true",
+                    help="skip the boundary-storage shot (reverse time stepping)")
     ap.add_argument("--batch", action="store_true",
                     help="also run the batched-shots leg (32 apertures, radius 8)")
     ap.add_argument("--batch-nt", type=int, default=1500)
@@ -436,6 +438,51 @@ def revolve_leg(w, slots, vel, rec, dobs, dev):
     return res
 
 
+def boundary_leg(w, vel, rec, dobs, dev, ref_image, ref_shot_s, ref_ws_gb):
+    """One shot of the main workload with boundary storage: the forward pass
+    keeps the model region's boundary band of every state, the backward pass
+    recovers the source field by reverse time stepping (no recompute pass).
+    CUDA events around the shot; the image is compared with the checkpoint
+    image of the timed run."""
+    import torch
+
+    import paper_1603_03971_gb300 as rtm
+
+    p = rtm.params_for(w, storage="boundary")
+    ws = rtm.alloc_workspace(p, dev)
+    c = rtm.model_prep(p, vel, ws)
+    img = torch.zeros((p.nz, p.ny, p.nx), dtype=torch.float32, device=dev)
+    rtm.shot(p, c, rec, dobs, ws, img)  # warm-up
+    img.zero_()
+    rtm.reset_stats()
+    rtm.set_timing(True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    rtm.shot(p, c, rec, dobs, ws, img)
+    ev[1].record()
+    torch.cuda.synchronize()
+    rtm.set_timing(False)
+    st = rtm.stats()
+    rtm.check(ws)
+    t = ev[0].elapsed_time(ev[1]) / 1e3
+    num = float(torch.linalg.vector_norm((img - ref_image).double()))
+    den = float(torch.linalg.vector_norm(ref_image.double()))
+    NZ, NY, NX = w.padded_shape
+    modes = {k: {"ms_per_launch": v["ms"] / v["launches"],
+                 "gbs": v["bytes"] / v["ms"] / 1e6}
+             for k, v in st["stencil"].items() if v["launches"] and v["ms"] > 0}
+    # stencil updates: forward and receiver passes on the padded grid, the
+    # reverse pass on the model region (nt - 2 steps)
+    updates = 2 * p.nt * NX * NY * NZ + max(p.nt - 2, 0) * p.nx * p.ny * p.nz
+    res = {"shot_s": t, "shot_s_checkpoint": ref_shot_s, "speedup_vs_checkpoint": ref_shot_s / t,
+           "workspace_gb": ws.numel() / 1e9, "workspace_gb_checkpoint": ref_ws_gb,
+           "image_rel_l2_vs_checkpoint": num / den if den > 0 else None,
+           "gpoint_updates_per_s": updates / t / 1e9, "stencil_modes": modes}
+    del ws
+    return res
+
+
 def batch_leg(args, dev):
     """32 shots on seeded uneven apertures of a 1024 x 1024 x 512 layered /
     salt model, radius-8 stencil, each a full checkpointed RTM, in one
@@ -594,6 +641,12 @@ def run_ours(args):
     imaging_res = None
     if rank == 0 and args.imaging:
         imaging_res = imaging_leg(p, c, rec, dobs, ws, dev)
+    boundary_res = None
+    if rank == 0 and not args.no_boundary:
+        ref = image / float(args.warmup + args.steps)  # one shot's checkpoint image
+        boundary_res = boundary_leg(w, vel, rec, dobs, dev, ref, t_max / args.steps,
+                                    ws.numel() / 1e9)
+        del ref
     revolve_res = None
     if rank == 0 and args.revolve > 0:
         revolve_res = revolve_leg(w, args.revolve, vel, rec, dobs, dev)
@@ -629,7 +682,7 @@ def run_ours(args):
             "config": cfg, "shot_s": t_max / args.steps, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": st["launches"],
             "clocks": clocks, "impl": "ours", "learned": learned, "batch": batch_res,
-            "imaging": imaging_res, "revolve": revolve_res,
+            "imaging": imaging_res, "revolve": revolve_res, "boundary": boundary_res,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -67,7 +67,8 @@ typedef enum {
     RTM_ERR_STATE = 8        /* workspace prepared for another purpose */
 } rtm_status;
 
-enum { RTM_STORE_ALL = 0, RTM_STORE_CKPT = 1, RTM_STORE_LEARNED = 2, RTM_STORE_REVOLVE = 3 };
+enum { RTM_STORE_ALL = 0, RTM_STORE_CKPT = 1, RTM_STORE_LEARNED = 2, RTM_STORE_REVOLVE = 3,
+       RTM_STORE_BOUNDARY = 4 };
 enum { RTM_VEL_V = 0, RTM_VEL_V2 = 1 };
 
 typedef struct {
@@ -86,7 +87,11 @@ typedef struct {
                                RTM_STORE_LEARNED: an 8x autoencoder latent per
                                imaging snapshot (the *_learned calls);
                                RTM_STORE_REVOLVE: binomial checkpointing in a
-                               fixed number of slots (imaging only) */
+                               fixed number of slots (imaging only);
+                               RTM_STORE_BOUNDARY: the model region's boundary
+                               band of every state, the source wavefield
+                               recovered by reverse time stepping (imaging
+                               only; model sides above 2 radius) */
     int32_t ckpt_every;     /* steps per checkpoint segment (RTM_STORE_CKPT);
                                number of checkpoint slots (RTM_STORE_REVOLVE);
                                exact window (RTM_STORE_LEARNED): the imaging
@@ -100,10 +105,10 @@ typedef struct {
 /* Per-kernel-class device time, filled when timing is enabled. */
 typedef struct {
     int64_t launches;       /* kernel launches of this library since the last reset */
-    int64_t stencil_launches[6];  /* per stencil mode: fwd, fwd+snap, bwd+image,
-                                     fwd+Lu, bwd+grad, batched */
-    double stencil_ms[6];   /* summed CUDA-event time per stencil mode */
-    double stencil_bytes[6];/* summed algorithmic bytes per stencil mode */
+    int64_t stencil_launches[7];  /* per stencil mode: fwd, fwd+snap, bwd+image,
+                                     fwd+Lu, bwd+grad, batched, reverse */
+    double stencil_ms[7];   /* summed CUDA-event time per stencil mode */
+    double stencil_bytes[7];/* summed algorithmic bytes per stencil mode */
 } rtm_stats;
 
 /* Library version string. */
@@ -309,6 +314,27 @@ rtm_status rtm_ae_gemm_bf16(const uint16_t *d_A, const uint16_t *d_B, float *d_C
 int64_t rtm_revolve_cost(int32_t nstates, int32_t slots);
 int32_t rtm_revolve_schedule(int32_t nstates, int32_t slots, int32_t *h_actions,
                              int32_t max_actions);
+
+/* ---- boundary storage (RTM_STORE_BOUNDARY) ---------------------------------
+ * The receiver pass needs the source wavefield at the imaging steps in
+ * reverse order (Sec. I). Inside the model region the sponge factor is
+ * exactly 1, so the forward update u^{n+1} = 2u^n + c L u^n - u^{n-1} (+ the
+ * source term) can be solved for u^{n-1}: the same arithmetic with the two
+ * time levels swapped. rtm_forward keeps, for every state u^1 .. u^{nt-2},
+ * the model region's band of cells within r of one of its faces (their
+ * stencils reach into the sponge); the backward call starts from the last
+ * two states the forward call leaves in the workspace and steps the source
+ * field back in time next to the receiver field, one reverse step (model
+ * region only) per time step, taking the band cells from storage. No
+ * recompute pass and no snapshot slab; imaging reads the recovered field in
+ * place. Band storage per state:
+ *   2r nx ny + 2r (nz - 2r) nx + 2r (nz - 2r)(ny - 2r) floats
+ * (z-face planes, then y-face rows, then x-face cells). Needs nx, ny, nz >
+ * 2r; imaging only (want_grad = 0). The recovered field carries FP32
+ * rounding of the reverse steps (about 1e-6 relative over hundreds of
+ * steps); the receiver field and the source trace are those of the other
+ * storage modes bit for bit. rtm_backward_image must follow the rtm_forward
+ * of the same shot with nothing in between that writes the workspace. */
 
 /* ---- imaging-condition variants -------------------------------------------
  * The paper forms the image by zero-lag cross-correlation of the source and

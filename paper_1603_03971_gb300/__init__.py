@@ -16,8 +16,8 @@ from typing import Optional
 
 import torch
 
-from ._lib import (RTM_STORE_ALL, RTM_STORE_CKPT, RTM_STORE_LEARNED, RTM_STORE_REVOLVE,
-                   RTM_VEL_V, RTM_VEL_V2,
+from ._lib import (RTM_STORE_ALL, RTM_STORE_BOUNDARY, RTM_STORE_CKPT, RTM_STORE_LEARNED,
+                   RTM_STORE_REVOLVE, RTM_VEL_V, RTM_VEL_V2,
                    RtmError, RtmParams, RtmStats, call, lib)
 
 __all__ = [
@@ -41,7 +41,8 @@ def make_params(nx, ny, nz, nb, radius, nt, dx, dt, f0, t0, src, nrec, storage="
     p.src_x, p.src_y, p.src_z = (int(v) for v in src)
     p.nrec = int(nrec)
     p.storage = {"all": RTM_STORE_ALL, "ckpt": RTM_STORE_CKPT,
-                 "learned": RTM_STORE_LEARNED, "revolve": RTM_STORE_REVOLVE}[storage]
+                 "learned": RTM_STORE_LEARNED, "revolve": RTM_STORE_REVOLVE,
+                 "boundary": RTM_STORE_BOUNDARY}[storage]
     p.ckpt_every = int(ckpt_every)
     p.image_every = int(image_every)
     p.want_grad = 1 if want_grad else 0
@@ -273,7 +274,7 @@ def set_timing(enable: bool):
 def stats() -> dict:
     s = RtmStats()
     call("rtm_stats_get", ctypes.byref(s))
-    names = ["fwd", "fwd_snap", "bwd_image", "fwd_lu", "bwd_grad", "batch"]
+    names = ["fwd", "fwd_snap", "bwd_image", "fwd_lu", "bwd_grad", "batch", "rev"]
     return {
         "launches": int(s.launches),
         "stencil": {n: {"launches": int(s.stencil_launches[i]), "ms": float(s.stencil_ms[i]),

@@ -16,7 +16,7 @@ STATUS_NAMES = {
     4: "RTM_ERR_CUDA", 5: "RTM_ERR_TIMEOUT", 6: "RTM_ERR_NUMERIC", 7: "RTM_ERR_UNSUPPORTED",
     8: "RTM_ERR_STATE",
 }
-RTM_STORE_ALL, RTM_STORE_CKPT, RTM_STORE_LEARNED, RTM_STORE_REVOLVE = 0, 1, 2, 3
+RTM_STORE_ALL, RTM_STORE_CKPT, RTM_STORE_LEARNED, RTM_STORE_REVOLVE, RTM_STORE_BOUNDARY = 0, 1, 2, 3, 4
 RTM_VEL_V, RTM_VEL_V2 = 0, 1
 
 
@@ -47,9 +47,9 @@ class RtmParams(ctypes.Structure):
 class RtmStats(ctypes.Structure):
     _fields_ = [
         ("launches", ctypes.c_int64),
-        ("stencil_launches", ctypes.c_int64 * 6),
-        ("stencil_ms", ctypes.c_double * 6),
-        ("stencil_bytes", ctypes.c_double * 6),
+        ("stencil_launches", ctypes.c_int64 * 7),
+        ("stencil_ms", ctypes.c_double * 7),
+        ("stencil_bytes", ctypes.c_double * 7),
     ]
 
 

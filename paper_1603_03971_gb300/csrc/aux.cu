@@ -4,6 +4,7 @@
 
 #include <math.h>
 
+#include "band.cuh"
 #include "rtm_internal.h"
 
 namespace rtm {
@@ -151,8 +152,31 @@ __global__ void k_image_finalize(Geometry G, const float* __restrict__ slab,
 
 // source illumination: illum[z][y][x] += u^2 of the model columns of a
 // snapshot slab [nz][ny][NX]; 16-byte vectors along x when both rows allow
+// boundary band of the model region: gather from a padded field / scatter into it
+__global__ void k_band_copy(Geometry G, int r, float* __restrict__ field,
+                            float* __restrict__ band, long long n, int to_field) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < n; b += stride) {
+        int mx, my, mz;
+        band_cell(b, G.nx, G.ny, G.nz, r, mx, my, mz);
+        const long long i =
+            ((long long)(mz + G.nb) * G.NY + (my + G.nb)) * G.NX + (mx + G.nb);
+        if (to_field)
+            field[i] = band[b];
+        else
+            band[b] = field[i];
+    }
+}
+
+// first element of model row zy = z ny + y: in the slab, or in a padded field
+__device__ __forceinline__ long long model_row(const Geometry& G, long long zy, int padded) {
+    if (!padded) return zy * G.NX + G.nb;
+    const long long z = zy / G.ny;
+    return ((z + G.nb) * G.NY + (zy - z * G.ny) + G.nb) * G.NX + G.nb;
+}
+
 __global__ void k_illum_add(Geometry G, const float* __restrict__ slab,
-                            float* __restrict__ illum, int vec) {
+                            float* __restrict__ illum, int vec, int padded) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     if (vec) {
         const int nx4 = G.nx >> 2;
@@ -160,7 +184,8 @@ __global__ void k_illum_add(Geometry G, const float* __restrict__ slab,
         for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
             const long long zy = i / nx4;
             const int x4 = (int)(i - zy * nx4);
-            const float4 u = __ldcs(reinterpret_cast<const float4*>(slab + zy * G.NX + G.nb) + x4);
+            const float4 u =
+                __ldcs(reinterpret_cast<const float4*>(slab + model_row(G, zy, padded)) + x4);
             float4* d = reinterpret_cast<float4*>(illum + zy * G.nx) + x4;
             float4 a = *d;
             a.x = fmaf(u.x, u.x, a.x);
@@ -175,7 +200,7 @@ __global__ void k_illum_add(Geometry G, const float* __restrict__ slab,
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const long long zy = i / G.nx;
         const int x = (int)(i % G.nx);
-        const float u = slab[zy * G.NX + x + G.nb];
+        const float u = slab[model_row(G, zy, padded) + x];
         illum[i] = fmaf(u, u, illum[i]);
     }
 }
@@ -333,15 +358,23 @@ cudaError_t launch_image_finalize(const Geometry& G, const float* slab, float* i
     return cudaGetLastError();
 }
 
-cudaError_t launch_illum_add(const Geometry& G, const float* slab, float* illum,
+cudaError_t launch_band_copy(const Geometry& G, int r, float* field, float* band, int to_field,
+                             cudaStream_t s) {
+    const long long n = band_cells(G.nx, G.ny, G.nz, r);
+    if (n <= 0) return cudaSuccess;
+    k_band_copy<<<grid_for(n, 256), 256, 0, s>>>(G, r, field, band, n, to_field);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_illum_add(const Geometry& G, const float* slab, float* illum, int padded,
                              cudaStream_t s) {
     const long long n = (long long)G.nx * G.ny * G.nz;
-    // slab rows start 16-byte aligned (NX % 4 == 0); the model columns do
-    // when nb % 4 == 0, the illumination rows when nx % 4 == 0
+    // slab and padded rows start 16-byte aligned (NX % 4 == 0); the model
+    // columns do when nb % 4 == 0, the illumination rows when nx % 4 == 0
     const int vec = (G.nb % 4 == 0) && (G.nx % 4 == 0) &&
                     (reinterpret_cast<uintptr_t>(illum) % 16 == 0) &&
                     (reinterpret_cast<uintptr_t>(slab) % 16 == 0);
-    k_illum_add<<<grid_for(vec ? n / 4 : n, 256), 256, 0, s>>>(G, slab, illum, vec);
+    k_illum_add<<<grid_for(vec ? n / 4 : n, 256), 256, 0, s>>>(G, slab, illum, vec, padded);
     return cudaGetLastError();
 }
 

@@ -13,6 +13,7 @@
 
 #include "../../include/rtm.h"
 #include "ae_internal.h"
+#include "band.cuh"
 #include "revolve.h"
 #include "rtm_internal.h"
 
@@ -136,6 +137,8 @@ struct Layout {
     size_t snap = 0, nsnap = 0, snap_elems = 0;
     // learned storage: one latent and one scale per imaging step, codec scratch
     size_t latent = 0, latent_bytes = 0, scales = 0, ae_h = 0, ae_scalars = 0;
+    // boundary storage: the model region's band of the states u^1 .. u^{nt-2}
+    size_t band = 0, nband = 0, nbands = 0;
     size_t total = 0;
 };
 
@@ -199,6 +202,12 @@ Layout layout_of(const rtm_params* p) {
         L.nckpt = (size_t)(p->ckpt_every < M ? p->ckpt_every : M);
         L.ckpt = take(2 * fb * L.nckpt);
         L.nsnap = 1;  // the snapshot of the state being delivered
+    } else if (p->storage == RTM_STORE_BOUNDARY) {
+        // imaging reads the reconstructed field in place: no snapshot slab
+        L.nband = (size_t)band_cells(p->nx, p->ny, p->nz, p->radius);
+        L.nbands = p->nt > 2 ? (size_t)(p->nt - 2) : 0;
+        L.band = take(sizeof(float) * L.nband * (L.nbands ? L.nbands : 1));
+        L.nsnap = 0;
     } else {
         const int k = p->ckpt_every;
         const int nseg = (p->nt + k - 1) / k;
@@ -206,7 +215,8 @@ Layout layout_of(const rtm_params* p) {
         L.ckpt = take(2 * fb * L.nckpt);
         L.nsnap = (size_t)k;
     }
-    L.snap = take(sizeof(float) * L.snap_elems * (L.nsnap ? L.nsnap : 1));
+    if (p->storage != RTM_STORE_BOUNDARY)
+        L.snap = take(sizeof(float) * L.snap_elems * (L.nsnap ? L.nsnap : 1));
     L.total = off;
     return L;
 }
@@ -237,8 +247,18 @@ rtm_status validate(const rtm_params* p) {
                     p->src_y, p->src_z);
     if (p->nrec < 0) return fail(RTM_ERR_INVALID, "nrec %d < 0", p->nrec);
     if (p->storage != RTM_STORE_ALL && p->storage != RTM_STORE_CKPT &&
-        p->storage != RTM_STORE_LEARNED && p->storage != RTM_STORE_REVOLVE)
+        p->storage != RTM_STORE_LEARNED && p->storage != RTM_STORE_REVOLVE &&
+        p->storage != RTM_STORE_BOUNDARY)
         return fail(RTM_ERR_INVALID, "storage %d unknown", p->storage);
+    if (p->storage == RTM_STORE_BOUNDARY) {
+        if (p->want_grad)
+            return fail(RTM_ERR_INVALID, "boundary storage serves imaging, not the gradient");
+        const int r2 = 2 * p->radius;
+        if (p->nx <= r2 || p->ny <= r2 || p->nz <= r2)
+            return fail(RTM_ERR_INVALID,
+                        "boundary storage needs model sides above 2 r = %d (got %dx%dx%d)", r2,
+                        p->nx, p->ny, p->nz);
+    }
     if (p->storage == RTM_STORE_REVOLVE) {
         if (p->want_grad)
             return fail(RTM_ERR_INVALID, "binomial checkpointing serves imaging, not the gradient");
@@ -291,6 +311,8 @@ struct Ctx {
     int variant;
     const float* ae = nullptr;  // codec parameters (learned storage)
     float* illum = nullptr;     // source illumination, model grid (+=), or NULL
+    bool snap_padded = false;   // imaging snapshots are padded fields (boundary storage)
+    bool zchunk_auto = true;    // z-slab height chosen per launch region
 
     float* at(size_t off) const { return reinterpret_cast<float*>(ws + off); }
     ae::bf16* latent_slot(size_t k) const {
@@ -311,6 +333,8 @@ struct Ctx {
     float* ckpt_field(size_t j, int which) const {
         return at(L.ckpt) + ((j - 1) * 2 + which) * d.N;
     }
+    // band of state u^m, 1 <= m <= nt - 2 (boundary storage)
+    float* band_of(int m) const { return at(L.band) + (size_t)(m - 1) * L.nband; }
 };
 
 rtm_status make_ctx(Ctx& C, const rtm_params* p, const float* c, void* ws, rtm_stream s) {
@@ -347,11 +371,14 @@ rtm_status make_ctx(Ctx& C, const rtm_params* p, const float* c, void* ws, rtm_s
         zc = g_zchunk[p->radius];
         var = g_variant[p->radius];
     }
+    C.zchunk_auto = zc <= 0;
     C.base.zchunk = zc > 0 ? zc : auto_zchunk(p->radius, C.d.NX, C.d.NY, C.d.NZ);
     if ((C.d.NZ + C.base.zchunk - 1) / C.base.zchunk > 65535)
         C.base.zchunk = (C.d.NZ + 65534) / 65535;  // grid.z limit
     // automatic: TMA plane loads wherever the driver provides tensor maps
     C.variant = var != 0 ? var : (tma_available() ? 2 : 1);
+    C.snap_padded = p->storage == RTM_STORE_BOUNDARY;
+    set_region(C.base, MODE_FWD);
     return RTM_OK;
 }
 
@@ -363,6 +390,7 @@ double stencil_bytes(const Ctx& C, int mode) {
         case MODE_BWD_IMAGE: return 16.0 * N + 12.0 * M;
         case MODE_FWD_LU: return 20.0 * N;
         case MODE_BWD_GRAD: return 28.0 * N;
+        case MODE_REV: return 16.0 * M;
         default: return 0.0;
     }
 }
@@ -373,6 +401,10 @@ rtm_status stencil(Ctx& C, int mode, const float* cur, float* prev, float* snap,
     a.u_prev = prev;
     a.snap = snap;
     a.acc = acc;
+    set_region(a, mode);
+    if (mode == MODE_REV && C.zchunk_auto)  // slabs sized for the model region's tiles
+        a.zchunk = auto_zchunk(C.p->radius, a.xend - a.xorg, a.yend - a.yorg, a.zend - a.zorg);
+    a.snap_padded = (mode == MODE_BWD_IMAGE && C.snap_padded) ? 1 : 0;
     bool timing;
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -451,6 +483,11 @@ rtm_status run_forward(Ctx& C, const int32_t* rec, float* data, float* u_last) {
             }
         }
         CHECK(stencil(C, mode, cur, prev, snap, nullptr));
+        if (p->storage == RTM_STORE_BOUNDARY && n + 1 <= p->nt - 2) {
+            // the band of u^{n+1} (now in prev)
+            CU(launch_band_copy(C.G, p->radius, prev, C.band_of(n + 1), 0, C.s));
+            count_launch();
+        }
         if (p->storage == RTM_STORE_LEARNED && (n + 1) % ie == 0 && n + 1 > p->ckpt_every) {
             // the encoder reads u^{n+1} (now in prev) in place: no snapshot copy
             const size_t k = (size_t)((n + 1) / ie - 1);
@@ -571,7 +608,7 @@ rtm_status run_backward(Ctx& C, const int32_t* rec, const float* rdata, float* s
         CHECK(stencil(C, mode, mcur, mprev, mode == MODE_FWD ? nullptr : snap,
                       mode == MODE_FWD ? nullptr : acc));
         if (mode == MODE_BWD_IMAGE && C.illum) {
-            CU(launch_illum_add(C.G, snap, C.illum, C.s));
+            CU(launch_illum_add(C.G, snap, C.illum, C.snap_padded ? 1 : 0, C.s));
             count_launch();
         }
         float* t = mprev;
@@ -613,6 +650,28 @@ rtm_status run_backward(Ctx& C, const int32_t* rec, const float* rdata, float* s
         }
     } else if (p->storage == RTM_STORE_REVOLVE) {
         CHECK(run_revolve(C, rec, back_step));
+    } else if (p->storage == RTM_STORE_BOUNDARY) {
+        // the forward run leaves u^{nt} in f[(nt + 1) % 2] and u^{nt-1} in
+        // f[nt % 2]; each earlier state is recovered in the model region by
+        // the reverse step, in place over the state two steps later
+        float* hi = C.at(C.L.f[(p->nt + 1) % 2]);  // u^{m+1}
+        float* lo = C.at(C.L.f[p->nt % 2]);        // u^m
+        CHECK(back_step(p->nt, p->nt % ie == 0 ? hi : nullptr));
+        for (int m = p->nt - 1; m >= 1; m--) {
+            if (m <= p->nt - 2) {
+                // lo = u^{m+1}, hi = u^{m+2}: undo forward step m + 1 (its
+                // source injection is undone by the same pre-adjustment)
+                CHECK(fwd_aux(C, lo, hi, rec, nullptr, C.wav() + m + 1));
+                CHECK(stencil(C, MODE_REV, lo, hi, nullptr, nullptr));
+                // band cells: their stencils reach into the sponge; stored
+                CU(launch_band_copy(C.G, p->radius, hi, C.band_of(m), 1, C.s));
+                count_launch();
+                float* t = lo;
+                lo = hi;
+                hi = t;
+            }
+            CHECK(back_step(m, m % ie == 0 ? lo : nullptr));
+        }
     } else if (p->storage == RTM_STORE_ALL) {
         for (int m = p->nt; m >= 1; m--) {
             float* snap = nullptr;

@@ -16,7 +16,11 @@ enum StencilMode : int {
     MODE_BWD_IMAGE = 2, // + image slab += snapshot * new field
     MODE_FWD_LU = 3,    // + write L u on the padded grid (gradient snapshot)
     MODE_BWD_GRAD = 4,  // + grad += new field * snapshot (L u), padded grid
-    MODE_COUNT = 5
+    // (5: the batched launch, in the statistics only)
+    MODE_REV = 6,       // reverse step over the model region, sponge factor 1:
+                        // u^{n-1} = 2u^n + c L u^n - u^{n+1} (cells outside the
+                        // model keep their value)
+    MODE_COUNT = 7
 };
 
 constexpr int kMaxRadius = 8;
@@ -32,13 +36,35 @@ struct StepArgs {
     const float* gx;     // sponge profiles
     const float* gy;
     const float* gz;
-    float* snap;         // snapshot (mode dependent)
+    float* snap;         // snapshot or band of one state (mode dependent)
     float* acc;          // image slab or gradient accumulator
     int NX, NY, NZ;      // padded grid
     int nb, nx, ny, nz;  // model region
     int zchunk;          // z planes per thread block
+    // region the launch covers: x in [xorg, xend) (xorg % 4 == 0), y in
+    // [yorg, yend), z in [zorg, zend); the whole padded grid except for
+    // MODE_REV, which covers the model region
+    int xorg, xend, yorg, yend, zorg, zend;
+    int snap_padded;     // MODE_BWD_IMAGE: snapshot on the padded grid instead of the slab
     float a[kMaxRadius + 1];  // a[0] = 3 a0 / dx^2, a[k] = a_k / dx^2
 };
+
+// the region of a mode: the padded grid, or the model region for MODE_REV
+inline void set_region(StepArgs& a, int mode) {
+    if (mode == MODE_REV) {
+        a.xorg = a.nb & ~3;
+        a.xend = a.nb + a.nx;
+        a.yorg = a.nb;
+        a.yend = a.nb + a.ny;
+        a.zorg = a.nb;
+        a.zend = a.nb + a.nz;
+    } else {
+        a.xorg = a.yorg = a.zorg = 0;
+        a.xend = a.NX;
+        a.yend = a.NY;
+        a.zend = a.NZ;
+    }
+}
 
 cudaError_t launch_stencil(int radius, int mode, const StepArgs& a, cudaStream_t s);
 // the same step with TMA plane loads (tuning variant 2); status: device status word
@@ -84,7 +110,13 @@ struct LapWeights {
     int r;
     float a[kMaxRadius + 1];  // a[0] = 3 a0 / dx^2, a[k] = a_k / dx^2
 };
-cudaError_t launch_illum_add(const Geometry& G, const float* slab, float* illum, cudaStream_t s);
+// boundary band of the model region (band.cuh): gather it from a padded
+// field into band storage (to_field = 0) or scatter it back (to_field = 1)
+cudaError_t launch_band_copy(const Geometry& G, int r, float* field, float* band, int to_field,
+                             cudaStream_t s);
+// illum += u^2 over the model region; u: the model slab, or a padded field (padded = 1)
+cudaError_t launch_illum_add(const Geometry& G, const float* slab, float* illum, int padded,
+                             cudaStream_t s);
 cudaError_t launch_image_normalize(const float* image, const float* illum, long long n,
                                    unsigned int* max_bits, float eps_rel, float* out,
                                    cudaStream_t s);

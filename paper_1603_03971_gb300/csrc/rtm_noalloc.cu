@@ -143,6 +143,7 @@ extern "C" rtm_status rtm_forward_noalloc(const rtm_params* p, const float* d_c,
     A.nz = p->nz;
     A.zchunk = auto_zchunk(p->radius, NX, NY, NZ);
     if ((NZ + A.zchunk - 1) / A.zchunk > 65535) A.zchunk = (NZ + 65534) / 65535;
+    set_region(A, MODE_FWD);
 
     const long long src = ((long long)(p->src_z + p->nb) * NY + (p->src_y + p->nb)) * NX +
                           (p->src_x + p->nb);

@@ -28,11 +28,11 @@ __global__ void __launch_bounds__(256, R == 4 ? 2 : 1) k_stencil(const __grid_co
     __shared__ __align__(16) float sm[2][T::SH][T::SW];
 
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x0 = blockIdx.x * T::TX, y0 = blockIdx.y * T::TY;
+    const int x0 = A.xorg + blockIdx.x * T::TX, y0 = A.yorg + blockIdx.y * T::TY;
     const int x = x0 + 4 * tx;
     const int y = y0 + ty;
-    const int zb = blockIdx.z * A.zchunk;
-    const int ze = min(A.NZ, zb + A.zchunk);
+    const int zb = A.zorg + blockIdx.z * A.zchunk;
+    const int ze = min(A.zend, zb + A.zchunk);
     const bool xin = x < A.NX;  // NX % 4 == 0: a vector is all in or all out
     const bool yin = y < A.NY;
     const bool own = xin && yin;
@@ -59,6 +59,8 @@ __global__ void __launch_bounds__(256, R == 4 ? 2 : 1) k_stencil(const __grid_co
     const bool ym = (y >= A.nb) && (y < A.nb + A.ny);
     const size_t slab_col = (size_t)(y - A.nb) * A.NX + x;
     const size_t slab_plane = (size_t)A.ny * A.NX;
+    // reverse mode: all of this thread's cells lie in the model's x-y range
+    const bool model_col = x >= A.nb && x + 3 < A.nb + A.nx && y >= A.nb && y < A.nb + A.ny;
 
     // sponge factor of the column, gz per plane
     F4 gxy = zero4();
@@ -86,7 +88,7 @@ __global__ void __launch_bounds__(256, R == 4 ? 2 : 1) k_stencil(const __grid_co
         if constexpr (MODE == MODE_BWD_IMAGE) {
             if (own && xm && ym && z >= A.nb && z < A.nb + A.nz) {
                 const size_t o = (size_t)(z - A.nb) * slab_plane + slab_col;
-                s1 = ld_stream(A.snap + o);
+                s1 = ld_stream(A.snap + (A.snap_padded ? (size_t)z * plane + col : o));
                 s2 = ld_stream(A.acc + o);
             }
         } else if constexpr (MODE == MODE_BWD_GRAD) {
@@ -154,12 +156,26 @@ __global__ void __launch_bounds__(256, R == 4 ? 2 : 1) k_stencil(const __grid_co
                     lap.v[i] = fmaf(A.a[k], (px + py) + pz, lap.v[i]);
                 }
             }
-            const float gzv = A.gz[z];
             F4 out;
+            if constexpr (MODE == MODE_REV) {
+                // the sponge factor is 1 in the model region: the forward
+                // update with the two time levels swapped
 #pragma unroll
-            for (int i = 0; i < 4; i++) {
-                const float g = gxy.v[i] * gzv;
-                out.v[i] = g * fmaf(cc.v[i], lap.v[i], 2.0f * q[R].v[i]) - (g * g) * up.v[i];
+                for (int i = 0; i < 4; i++) out.v[i] = fmaf(cc.v[i], lap.v[i], 2.0f * q[R].v[i]) - up.v[i];
+                if (!model_col) {  // cells outside the model keep their value
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {
+                        const int mx = x + i - A.nb, my = y - A.nb;
+                        if (mx < 0 || mx >= A.nx || my < 0 || my >= A.ny) out.v[i] = up.v[i];
+                    }
+                }
+            } else {
+                const float gzv = A.gz[z];
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const float g = gxy.v[i] * gzv;
+                    out.v[i] = g * fmaf(cc.v[i], lap.v[i], 2.0f * q[R].v[i]) - (g * g) * up.v[i];
+                }
             }
             const size_t o = (size_t)z * plane + col;
             st_stream(A.u_prev + o, out);
@@ -201,8 +217,10 @@ template <int R, int MODE>
 cudaError_t launch_t(const StepArgs& a, cudaStream_t s) {
     using T = Tile<R>;
     dim3 block(T::BX, T::BY);
-    dim3 grid((a.NX + T::TX - 1) / T::TX, (a.NY + T::TY - 1) / T::TY,
-              (a.NZ + a.zchunk - 1) / a.zchunk);
+    dim3 grid((a.xend - a.xorg + T::TX - 1) / T::TX, (a.yend - a.yorg + T::TY - 1) / T::TY,
+              (a.zend - a.zorg + a.zchunk - 1) / a.zchunk);
+    if (a.xorg % 4 || a.xend <= a.xorg || a.yend <= a.yorg || a.zend <= a.zorg)
+        return cudaErrorInvalidValue;
     k_stencil<R, MODE><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -215,6 +233,7 @@ cudaError_t launch_r(int mode, const StepArgs& a, cudaStream_t s) {
         case MODE_BWD_IMAGE: return launch_t<R, MODE_BWD_IMAGE>(a, s);
         case MODE_FWD_LU: return launch_t<R, MODE_FWD_LU>(a, s);
         case MODE_BWD_GRAD: return launch_t<R, MODE_BWD_GRAD>(a, s);
+        case MODE_REV: return launch_t<R, MODE_REV>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -214,10 +214,10 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
     __shared__ int abort_flag;
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * T::BX + tx;
-    const int x0 = blockIdx.x * T::TX, y0 = blockIdx.y * T::TY;
+    const int x0 = A.xorg + blockIdx.x * T::TX, y0 = A.yorg + blockIdx.y * T::TY;
     const int x = x0 + V * tx, y = y0 + ty;
-    const int zb = blockIdx.z * A.zchunk;
-    const int ze = min(A.NZ, zb + A.zchunk);
+    const int zb = A.zorg + blockIdx.z * A.zchunk;
+    const int ze = min(A.zend, zb + A.zchunk);
     const bool own = x < A.NX && y < A.NY;
     const size_t plane = (size_t)A.NX * (size_t)A.NY;
     const size_t col = (size_t)y * A.NX + x;
@@ -225,6 +225,8 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
     const bool ym = (y >= A.nb) && (y < A.nb + A.ny);
     const size_t slab_col = (size_t)(y - A.nb) * A.NX + x;
     const size_t slab_plane = (size_t)A.ny * A.NX;
+    // reverse mode: all of this thread's cells lie in the model's x-y range
+    const bool model_col = x >= A.nb && x + V - 1 < A.nb + A.nx && y >= A.nb && y < A.nb + A.ny;
 
     if (tid == 0) {
         for (int s = 0; s < C::SU; s++) bar_init(&ubar[s]);
@@ -247,7 +249,10 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
         tma3(base, &M.prev, x0, y0, p, &abar[slot]);
         tma3(base + C::APLANE, &M.c, x0, y0, p, &abar[slot]);
         if constexpr (MODE == MODE_BWD_IMAGE) {
-            tma3(base + 2 * C::APLANE, &M.e1, x0, y0 - A.nb, p - A.nb, &abar[slot]);
+            if (A.snap_padded)
+                tma3(base + 2 * C::APLANE, &M.e1, x0, y0, p, &abar[slot]);
+            else
+                tma3(base + 2 * C::APLANE, &M.e1, x0, y0 - A.nb, p - A.nb, &abar[slot]);
             tma3(base + 3 * C::APLANE, &M.e2, x0, y0 - A.nb, p - A.nb, &abar[slot]);
         } else if constexpr (MODE == MODE_BWD_GRAD) {
             tma3(base + 2 * C::APLANE, &M.e1, x0, y0, p, &abar[slot]);
@@ -278,19 +283,19 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
     const int own_off = (R + ty) * T::SW + R + V * tx;  // this vector in a u^n plane
     const int aux_off = ty * T::TX + V * tx;             // this vector in an aux plane
 
+    // ring slots and mbarrier phases, advanced by counting
+    int sc = 0, pc = 0;                          // centre plane z
+    int shd = R % C::SU, phd = (R / C::SU) & 1;  // queue head plane z + R
+    int sa = 0, pa = 0;                          // pointwise operands of plane z
     for (int z = zb; z < ze; z++) {
         if (tid == 0 && !abort_flag) {
             if (z + R + kPrefetch <= last_u) issue_u(z + R + kPrefetch);
             if (z + kPrefetch < ze) issue_a(z + kPrefetch);
         }
-        const int ph = z + R;  // queue head plane
-        const int sh = (ph - zb) % C::SU;
-        bool ok = bar_wait(&ubar[sh], (uint32_t)(((ph - zb) / C::SU) & 1), &abort_flag);
-        q[2 * R] = vlds<V>(uring + sh * C::UPLANE + own_off);
-        const int sc = (z - zb) % C::SU;
-        ok = bar_wait(&ubar[sc], (uint32_t)(((z - zb) / C::SU) & 1), &abort_flag) && ok;
-        const int sa = (z - zb) % C::SA;
-        ok = bar_wait(&abar[sa], (uint32_t)(((z - zb) / C::SA) & 1), &abort_flag) && ok;
+        bool ok = bar_wait(&ubar[shd], (uint32_t)phd, &abort_flag);
+        q[2 * R] = vlds<V>(uring + shd * C::UPLANE + own_off);
+        ok = bar_wait(&ubar[sc], (uint32_t)pc, &abort_flag) && ok;
+        ok = bar_wait(&abar[sa], (uint32_t)pa, &abort_flag) && ok;
         const float* S = uring + sc * C::UPLANE;
         const float* aux = aring + sa * NA * C::APLANE;
 
@@ -363,11 +368,26 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
             const VT up = vlds<V>(aux + aux_off);
             const VT cc = vlds<V>(aux + C::APLANE + aux_off);
             const float gzv = A.gz[z];
+            const VT& qc = q[R];
             VT out;
+            if constexpr (MODE == MODE_REV) {
+                // the sponge factor is 1 in the model region: the forward
+                // update with the two time levels swapped
 #pragma unroll
-            for (int i = 0; i < V; i++) {
-                const float g = gxy.v[i] * gzv;
-                out.v[i] = g * fmaf(cc.v[i], lap.v[i], 2.0f * q[R].v[i]) - (g * g) * up.v[i];
+                for (int i = 0; i < V; i++) out.v[i] = fmaf(cc.v[i], lap.v[i], 2.0f * qc.v[i]) - up.v[i];
+                if (!model_col) {  // cells outside the model keep their value
+#pragma unroll
+                    for (int i = 0; i < V; i++) {
+                        const int mx = x + i - A.nb, my = y - A.nb;
+                        if (mx < 0 || mx >= A.nx || my < 0 || my >= A.ny) out.v[i] = up.v[i];
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < V; i++) {
+                    const float g = gxy.v[i] * gzv;
+                    out.v[i] = g * fmaf(cc.v[i], lap.v[i], 2.0f * qc.v[i]) - (g * g) * up.v[i];
+                }
             }
             const size_t o = (size_t)z * plane + col;
             vst_stream<V>(A.u_prev + o, out);
@@ -393,6 +413,9 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
             }
         }
         __syncthreads();  // every thread is done with planes z (centre, aux): slots reusable
+        if (++sc == C::SU) sc = 0, pc ^= 1;
+        if (++shd == C::SU) shd = 0, phd ^= 1;
+        if (++sa == C::SA) sa = 0, pa ^= 1;
 #pragma unroll
         for (int i = 0; i < 2 * R; i++) q[i] = q[i + 1];
     }
@@ -444,15 +467,20 @@ cudaError_t launch_tma_t(const StepArgs& a, int* status, cudaStream_t s) {
     if ((e = make_map(&M.prev, a.u_prev, a.NX, a.NY, a.NZ, T::TX, T::TY)) != cudaSuccess) return e;
     if ((e = make_map(&M.c, a.c, a.NX, a.NY, a.NZ, T::TX, T::TY)) != cudaSuccess) return e;
     if (MODE == MODE_BWD_IMAGE) {
-        if ((e = make_map(&M.e1, a.snap, a.NX, a.ny, a.nz, T::TX, T::TY)) != cudaSuccess) return e;
+        if ((e = a.snap_padded ? make_map(&M.e1, a.snap, a.NX, a.NY, a.NZ, T::TX, T::TY)
+                               : make_map(&M.e1, a.snap, a.NX, a.ny, a.nz, T::TX, T::TY)) !=
+            cudaSuccess)
+            return e;
         if ((e = make_map(&M.e2, a.acc, a.NX, a.ny, a.nz, T::TX, T::TY)) != cudaSuccess) return e;
     } else if (MODE == MODE_BWD_GRAD) {
         if ((e = make_map(&M.e1, a.snap, a.NX, a.NY, a.NZ, T::TX, T::TY)) != cudaSuccess) return e;
         if ((e = make_map(&M.e2, a.acc, a.NX, a.NY, a.NZ, T::TX, T::TY)) != cudaSuccess) return e;
     }
     dim3 block(T::BX, T::BY);
-    dim3 grid((a.NX + T::TX - 1) / T::TX, (a.NY + T::TY - 1) / T::TY,
-              (a.NZ + a.zchunk - 1) / a.zchunk);
+    dim3 grid((a.xend - a.xorg + T::TX - 1) / T::TX, (a.yend - a.yorg + T::TY - 1) / T::TY,
+              (a.zend - a.zorg + a.zchunk - 1) / a.zchunk);
+    if (a.xorg % 4 || a.xend <= a.xorg || a.yend <= a.yorg || a.zend <= a.zorg)
+        return cudaErrorInvalidValue;
     k_stencil_tma<R, MODE><<<grid, block, smem, s>>>(a, M, status);
     return cudaGetLastError();
 }
@@ -465,6 +493,7 @@ cudaError_t launch_tma_r(int mode, const StepArgs& a, int* status, cudaStream_t 
         case MODE_BWD_IMAGE: return launch_tma_t<R, MODE_BWD_IMAGE>(a, status, s);
         case MODE_FWD_LU: return launch_tma_t<R, MODE_FWD_LU>(a, status, s);
         case MODE_BWD_GRAD: return launch_tma_t<R, MODE_BWD_GRAD>(a, status, s);
+        case MODE_REV: return launch_tma_t<R, MODE_REV>(a, status, s);
         default: return cudaErrorInvalidValue;
     }
 }

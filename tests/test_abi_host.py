@@ -65,6 +65,8 @@ def test_valid_params_pass():
     (dict(src=(-7, 0, 0)), 1), (dict(src=(0, 30, 0)), 1), (dict(nrec=-1), 1),
     (dict(storage="ckpt", ckpt_every=0), 1), (dict(image_every=0), 1),
     (dict(want_grad=True, image_every=2), 1),
+    (dict(storage="boundary", want_grad=True), 1),
+    (dict(storage="boundary", nz=8), 1),  # model sides must exceed 2 r = 8
 ])
 def test_invalid_params_rejected(change, code):
     p = _p(**change)
@@ -141,3 +143,9 @@ def test_workspace_sizes_follow_the_storage_policy():
     g = rtm.workspace_size(_p(nt=nt, want_grad=True))
     assert g >= 4 * (5 * N + nt * N)
     assert rtm.host_workspace_size(_p()) > all_
+    # boundary storage: the band of u^1 .. u^{nt-2} and no snapshot slab
+    r = 4
+    band = 2 * r * nx * ny + 2 * r * (nz - 2 * r) * nx + 2 * r * (nz - 2 * r) * (ny - 2 * r)
+    assert band == nx * ny * nz - (nx - 2 * r) * (ny - 2 * r) * (nz - 2 * r)
+    b = rtm.workspace_size(_p(nt=nt, storage="boundary"))
+    assert 4 * (4 * N + slab + (nt - 2) * band) <= b < 4 * (4 * N + slab + (nt - 2) * band) + 64 * 256
