@@ -7,7 +7,8 @@
 // arrive as zeros, the Dirichlet ghost cells) and P + 1 planes of the
 // pointwise operands (u^{n-1}, c, and the snapshot / accumulator of the
 // backward modes). Each ring slot has an mbarrier that the copy completes
-// (expect-tx); P = 2 planes are in flight ahead of the one being computed.
+// (expect-tx); P planes (one or two) are in flight ahead of the one being
+// computed.
 // Each thread keeps the 2r + 1 column values of its 4-point vector in a
 // register queue, whose head it reads from the newest u^n plane in shared
 // memory. One block barrier per plane frees the slots for refilling.
@@ -31,11 +32,10 @@ namespace rtm {
 
 namespace {
 
-constexpr int kPrefetch = 2;
 constexpr long long kTmaWaitLimit = 1LL << 26;
 
 struct TmaMaps {
-    CUtensorMap u, prev, c, e1, e2;
+    CUtensorMap u, prev, c, e1, e2, uh;  // uh: u^n without halo (queue heads)
 };
 
 // V consecutive x points per thread: 4 (16-byte vectors) at radius 4; 2 at
@@ -142,14 +142,41 @@ __host__ __device__ constexpr bool split_chains() {
     return R == 8;
 }
 
-template <int R, int NA>
+template <int MODE>
+__host__ __device__ constexpr int aux_planes() {
+    return (MODE == MODE_BWD_IMAGE || MODE == MODE_BWD_GRAD) ? 4 : 2;
+}
+
+// u^n ring layout. Joint: the ring holds planes z .. z + r + P with their
+// halo; plane z + r is the queue head, and it stays in the ring until it is
+// the centre plane. Split (radius 8): the ring holds only the P + 1 centre
+// planes with their halo, and the queue head (plane z + r, the tile without
+// halo) travels with the pointwise operands of plane z: each plane is copied
+// twice from L2, but the ring shrinks from 2r + P + 1 halo planes (66 KB at
+// radius 8) to P + 1 (18 KB), so three blocks fit per SM in every mode
+template <int R, int MODE>
+__host__ __device__ constexpr bool split_ring() {
+    return R == 8 || aux_planes<MODE>() == 4;
+}
+
+// planes loaded ahead of the one being computed
+template <int R, int MODE>
+__host__ __device__ constexpr int tma_prefetch() {
+    return (R == 4 && aux_planes<MODE>() == 4) ? 1 : 2;
+}
+
+template <int R, int MODE>
 struct TmaCfg {
     using T = TmaTile<R, points_per_thread<R>()>;
-    static constexpr int SU = R + kPrefetch + 1;
-    static constexpr int SA = kPrefetch + 1;
+    static constexpr bool SPLIT = split_ring<R, MODE>();
+    static constexpr int NA = aux_planes<MODE>();
+    static constexpr int NAH = NA + (SPLIT ? 1 : 0);  // aux ring entries per plane
+    static constexpr int P = tma_prefetch<R, MODE>();
+    static constexpr int SU = SPLIT ? P + 1 : R + P + 1;
+    static constexpr int SA = P + 1;
     static constexpr int UPLANE = T::SH * T::SW;  // floats
     static constexpr int APLANE = T::TY * T::TX;
-    static constexpr int SMEM = (SU * UPLANE + SA * NA * APLANE) * 4;
+    static constexpr int SMEM = (SU * UPLANE + SA * NAH * APLANE) * 4;
 };
 
 __device__ __forceinline__ uint32_t s_u32(const void* p) {
@@ -188,14 +215,18 @@ __device__ __forceinline__ void tma3(float* dst, const CUtensorMap* map, int x, 
         : "memory");
 }
 
-// resident blocks per SM: with two pointwise operand rings (the forward
-// modes) a radius-4 block needs 73 KB of shared memory, so three fit when the
-// registers are capped at 80 per thread; the backward modes (four rings,
-// 98 KB) fit two
+// resident blocks per SM, with the registers capped at 80 per thread for
+// three: at radius 4 the forward modes need 73 KB of shared memory (three
+// fit), the backward modes 98 KB (two); at radius 8 the split ring needs
+// 36-48 KB (three)
 template <int R, int MODE>
 constexpr int tma_min_blocks() {
-    // radius 8 (two points per thread): 78-92 KB, two blocks
-    return R != 4 ? 2 : ((MODE == MODE_BWD_IMAGE || MODE == MODE_BWD_GRAD) ? 2 : 3);
+    return 3;
+}
+// the rings of the resident blocks fit the SM's 228 KB (1 KB reserved per block)
+template <int R, int MODE>
+constexpr bool rings_fit() {
+    return tma_min_blocks<R, MODE>() * (TmaCfg<R, MODE>::SMEM + 1024 + 256) <= 228 * 1024;
 }
 
 template <int R, int MODE>
@@ -204,8 +235,8 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
     constexpr int V = points_per_thread<R>();
     using T = TmaTile<R, V>;
     using VT = Vec<V>;
-    constexpr int NA = (MODE == MODE_BWD_IMAGE || MODE == MODE_BWD_GRAD) ? 4 : 2;
-    using C = TmaCfg<R, NA>;
+    using C = TmaCfg<R, MODE>;
+    constexpr int NA = C::NA;
     extern __shared__ __align__(128) float dsm[];
     float* uring = dsm;
     float* aring = dsm + C::SU * C::UPLANE;
@@ -236,7 +267,9 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
     }
     __syncthreads();
 
-    const int last_u = ze - 1 + R;  // newest u^n plane needed (queue head of the last step)
+    // newest u^n plane copied with its halo: the queue head of the last step
+    // (joint ring) or the last centre plane (split ring)
+    const int last_u = C::SPLIT ? ze - 1 : ze - 1 + R;
     auto issue_u = [&](int p) {
         const int slot = (p - zb) % C::SU;
         bar_expect(&ubar[slot], C::UPLANE * 4);
@@ -244,10 +277,11 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
     };
     auto issue_a = [&](int p) {
         const int slot = (p - zb) % C::SA;
-        float* base = aring + slot * NA * C::APLANE;
-        bar_expect(&abar[slot], NA * C::APLANE * 4);
+        float* base = aring + slot * C::NAH * C::APLANE;
+        bar_expect(&abar[slot], C::NAH * C::APLANE * 4);
         tma3(base, &M.prev, x0, y0, p, &abar[slot]);
         tma3(base + C::APLANE, &M.c, x0, y0, p, &abar[slot]);
+        if constexpr (C::SPLIT) tma3(base + NA * C::APLANE, &M.uh, x0, y0, p + R, &abar[slot]);
         if constexpr (MODE == MODE_BWD_IMAGE) {
             if (A.snap_padded)
                 tma3(base + 2 * C::APLANE, &M.e1, x0, y0, p, &abar[slot]);
@@ -260,8 +294,8 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
         }
     };
     if (tid == 0) {
-        for (int p = zb; p < zb + R + kPrefetch && p <= last_u; p++) issue_u(p);
-        for (int p = zb; p < zb + kPrefetch && p < ze; p++) issue_a(p);
+        for (int p = zb; p < zb + (C::SPLIT ? 0 : R) + C::P && p <= last_u; p++) issue_u(p);
+        for (int p = zb; p < zb + C::P && p < ze; p++) issue_a(p);
     }
 
     VT gxy = vzero<V>();
@@ -289,15 +323,20 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
     int sa = 0, pa = 0;                          // pointwise operands of plane z
     for (int z = zb; z < ze; z++) {
         if (tid == 0 && !abort_flag) {
-            if (z + R + kPrefetch <= last_u) issue_u(z + R + kPrefetch);
-            if (z + kPrefetch < ze) issue_a(z + kPrefetch);
+            const int pu = z + (C::SPLIT ? 0 : R) + C::P;
+            if (pu <= last_u) issue_u(pu);
+            if (z + C::P < ze) issue_a(z + C::P);
         }
-        bool ok = bar_wait(&ubar[shd], (uint32_t)phd, &abort_flag);
-        q[2 * R] = vlds<V>(uring + shd * C::UPLANE + own_off);
+        bool ok = true;
+        if constexpr (!C::SPLIT) {
+            ok = bar_wait(&ubar[shd], (uint32_t)phd, &abort_flag);
+            q[2 * R] = vlds<V>(uring + shd * C::UPLANE + own_off);
+        }
         ok = bar_wait(&ubar[sc], (uint32_t)pc, &abort_flag) && ok;
         ok = bar_wait(&abar[sa], (uint32_t)pa, &abort_flag) && ok;
         const float* S = uring + sc * C::UPLANE;
-        const float* aux = aring + sa * NA * C::APLANE;
+        const float* aux = aring + sa * C::NAH * C::APLANE;
+        if constexpr (C::SPLIT) q[2 * R] = vlds<V>(aux + NA * C::APLANE + aux_off);
 
         if (own && ok) {
             float v[V + 2 * R];
@@ -446,8 +485,8 @@ cudaError_t make_map(CUtensorMap* m, const float* base, int nx, int ny, int nz, 
 template <int R, int MODE>
 cudaError_t launch_tma_t(const StepArgs& a, int* status, cudaStream_t s) {
     using T = TmaTile<R, points_per_thread<R>()>;
-    constexpr int NA = (MODE == MODE_BWD_IMAGE || MODE == MODE_BWD_GRAD) ? 4 : 2;
-    constexpr int smem = TmaCfg<R, NA>::SMEM;
+    constexpr int smem = TmaCfg<R, MODE>::SMEM;
+    static_assert(rings_fit<R, MODE>(), "rings do not fit the resident blocks");
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_stencil_tma<R, MODE>,
@@ -465,6 +504,9 @@ cudaError_t launch_tma_t(const StepArgs& a, int* status, cudaStream_t s) {
     if ((e = make_map(&M.u, a.u_cur, a.NX, a.NY, a.NZ, T::TX + 2 * R, T::TY + 2 * R)) != cudaSuccess)
         return e;
     if ((e = make_map(&M.prev, a.u_prev, a.NX, a.NY, a.NZ, T::TX, T::TY)) != cudaSuccess) return e;
+    if (TmaCfg<R, MODE>::SPLIT &&
+        (e = make_map(&M.uh, a.u_cur, a.NX, a.NY, a.NZ, T::TX, T::TY)) != cudaSuccess)
+        return e;
     if ((e = make_map(&M.c, a.c, a.NX, a.NY, a.NZ, T::TX, T::TY)) != cudaSuccess) return e;
     if (MODE == MODE_BWD_IMAGE) {
         if ((e = a.snap_padded ? make_map(&M.e1, a.snap, a.NX, a.NY, a.NZ, T::TX, T::TY)
