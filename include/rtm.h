@@ -383,7 +383,11 @@ rtm_status rtm_image_filter(const rtm_params *p, const float *d_image, const flo
  *   d_data  modelled data in the same layout, or NULL.
  *   d_image [nz][ny][nx] of the full model, ACCUMULATED: each shot adds its
  *           image at its aperture, in shot order (deterministic).
- *   zchunk  z planes per work item (0: automatic). */
+ *   zchunk  z planes per work item (0: 128).
+ * The work items march their tiles with TMA plane loads when the driver
+ * provides tensor maps and rtm_set_tuning has not selected the vector-load
+ * variant (1) for the radius; both kernels give the same image within the
+ * wavefield tolerance. */
 typedef struct {
     int32_t ox, oy, oz;          /* aperture origin in the full model */
     int32_t nx, ny, nz;          /* aperture size */

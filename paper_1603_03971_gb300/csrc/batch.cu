@@ -68,7 +68,6 @@ __device__ void process_item(const BatchArgs& A, const BatchShot& S, const Batch
     const bool xin = x < S.NX, yin = y < S.NY, own = xin && yin;
     const size_t plane = (size_t)S.NX * S.NY;
     const size_t col = (size_t)y * S.NX + x;
-    const size_t N = plane * S.NZ;
 
     // buffers of this phase step
     const float* cur;
@@ -85,8 +84,8 @@ __device__ void process_item(const BatchArgs& A, const BatchShot& S, const Batch
         zero_in = (n == 0);
         if ((n + 1) % A.ckpt_every == 0 && n + 1 < A.nt) {
             const size_t j = (size_t)((n + 1) / A.ckpt_every);
-            ck_a = S.ckpt + ((j - 1) * 2 + 0) * N;
-            ck_b = S.ckpt + ((j - 1) * 2 + 1) * N;
+            ck_a = S.ckpt + ((j - 1) * 2 + 0) * S.fstride;
+            ck_b = S.ckpt + ((j - 1) * 2 + 1) * S.fstride;
         }
     } else if (ph.kind == PH_REC) {
         float *a, *b;
@@ -95,20 +94,20 @@ __device__ void process_item(const BatchArgs& A, const BatchShot& S, const Batch
             b = S.f1;
             zero_in = (ph.local == 0);
         } else {
-            a = S.ckpt + ((size_t)(ph.seg - 1) * 2 + 0) * N;
-            b = S.ckpt + ((size_t)(ph.seg - 1) * 2 + 1) * N;
+            a = S.ckpt + ((size_t)(ph.seg - 1) * 2 + 0) * S.fstride;
+            b = S.ckpt + ((size_t)(ph.seg - 1) * 2 + 1) * S.fstride;
         }
         cur = (ph.local & 1) ? a : b;
         prev = (ph.local & 1) ? b : a;
         if ((ph.step + 1) % A.image_every == 0)
-            snap_w = S.snap + (size_t)ph.local * ((size_t)S.nz * S.ny * S.NX);
+            snap_w = S.snap + (size_t)ph.local * S.sstride;
     } else {
         const int bi = A.nt - ph.step;  // 0 for m = nt
         cur = (bi & 1) ? S.m0 : S.m1;
         prev = (bi & 1) ? S.m1 : S.m0;
         zero_in = (ph.step == A.nt);
         if (ph.step % A.image_every == 0)
-            snap_r = S.snap + (size_t)ph.local * ((size_t)S.nz * S.ny * S.NX);
+            snap_r = S.snap + (size_t)ph.local * S.sstride;
     }
     // zero inputs: the first step of a recursion reads nothing and clears the
     // buffer that holds the step before it

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <memory>
 #include <vector>
 
 #include "../../include/rtm.h"
@@ -16,6 +17,33 @@ using namespace rtm;
 namespace {
 
 constexpr size_t kAlB = 256;
+// automatic z-slab height of a work item, per wave: the tallest slab (the
+// whole column first) that still gives every phase step at least
+// kItemsPerBlock items per resident block. Each step of a shot waits for all
+// items of its previous step, so too few items leave blocks idle at every
+// step; too short slabs repeat the 2r-plane queue warm-up. Measured with the
+// TMA kernel: 4 shots of 256 x 256 x 320 padded, whole columns / 256 / 128
+// planes: 137 / 174 / 270 Gpoint-updates/s (radius 4); the 32-shot radius-8
+// workload: whole columns 173.8, 128 planes 167.4
+constexpr int kBatchZchunk = 128;  // the workspace's sizing value
+constexpr int kItemsPerBlock = 3;
+
+int wave_zchunk(const std::vector<BatchShot>& shots, int first, int last, int grid) {
+    int nzmax = 1;
+    for (int i = first; i < last; i++) nzmax = std::max(nzmax, shots[i].NZ);
+    const int cand[] = {nzmax, 512, 384, 256, 192, 128, 96, 64};
+    int best = 64;
+    for (int zc : cand) {
+        if (zc > nzmax) continue;
+        long long items = 0;
+        for (int i = first; i < last; i++)
+            items += (long long)shots[i].tiles_x * shots[i].tiles_y *
+                     ((shots[i].NZ + zc - 1) / zc);
+        if (items >= (long long)kItemsPerBlock * grid) return zc;
+        best = zc;
+    }
+    return best;
+}
 double g_wait_seconds = 20.0;  // bound of each inter-block wait
 int g_poison_shot = -1;
 constexpr int kMaxShotsTotal = 1024;
@@ -84,8 +112,13 @@ rtm_status check_batch(const rtm_params* p, int nshots, const rtm_aperture* sh) 
     return RTM_OK;
 }
 
+// the batched kernel: TMA plane loads wherever the driver provides tensor maps
+// (unless the vector-load variant is selected for the radius)
+bool batch_uses_tma(int radius) { return tma_available() && tuning_variant(radius) != 1; }
+
 Plan make_plan(const rtm_params* p, int nshots, const rtm_aperture* sh, size_t budget,
                int zchunk) {
+    const int tile_x = batch_uses_tma(p->radius) ? batch_tma_tile_x(p->radius) : 64;
     Plan P;
     const int R = p->radius, k = p->ckpt_every, nt = p->nt;
     const int nseg = (nt + k - 1) / k;
@@ -100,7 +133,7 @@ Plan make_plan(const rtm_params* p, int nshots, const rtm_aperture* sh, size_t b
         b.NX = b.nx + 2 * p->nb;
         b.NY = b.ny + 2 * p->nb;
         b.NZ = b.nz + 2 * p->nb;
-        b.tiles_x = (b.NX + 63) / 64;
+        b.tiles_x = (b.NX + tile_x - 1) / tile_x;
         b.tiles_y = (b.NY + 15) / 16;
         b.tiles_z = (b.NZ + zchunk - 1) / zchunk;
         b.ntiles = b.tiles_x * b.tiles_y * b.tiles_z;
@@ -110,12 +143,10 @@ Plan make_plan(const rtm_params* p, int nshots, const rtm_aperture* sh, size_t b
         b.rec_z = sh[s].rec_z + p->nb;
         const size_t N = (size_t)b.NX * b.NY * b.NZ;
         const size_t slab = (size_t)b.nz * b.ny * b.NX;
-        size_t bytes = upb(4 * N);                                       // c
-        bytes += upb(4 * (size_t)b.NX) + upb(4 * (size_t)b.NY) + upb(4 * (size_t)b.NZ);
-        bytes += 4 * upb(4 * N);                                         // fields
-        bytes += upb(4 * N * 2 * (size_t)(nseg > 1 ? nseg - 1 : 0));     // checkpoints
-        bytes += upb(4 * slab * (size_t)k);                              // snapshots
-        bytes += upb(4 * slab);                                          // image slab
+        size_t bytes = upb(4 * (size_t)b.NX) + upb(4 * (size_t)b.NY) + upb(4 * (size_t)b.NZ);
+        // c, two field pairs and the checkpoints, one stride apart
+        bytes += upb(4 * N) * (5 + 2 * (size_t)(nseg > 1 ? nseg - 1 : 0));
+        bytes += upb(4 * slab) * ((size_t)k + 1);  // snapshots and the image slab
         P.shots.push_back(b);
         P.bytes.push_back(bytes);
         P.data_off.push_back(doff);
@@ -174,7 +205,7 @@ rtm_status rtm_batch_set_wait(double seconds, int32_t poison_shot) {
 size_t rtm_batch_workspace_size(const rtm_params* p, int32_t nshots, const rtm_aperture* h_shots,
                                 size_t budget_bytes) {
     if (!p || check_batch(p, nshots, h_shots) != RTM_OK) return 0;
-    return make_plan(p, nshots, h_shots, budget_bytes, auto_zchunk(p->radius, 64, 16, 1 << 20))
+    return make_plan(p, nshots, h_shots, budget_bytes, kBatchZchunk)
         .total;
 }
 
@@ -187,18 +218,8 @@ rtm_status rtm_batch(const rtm_params* p, int32_t nshots, const rtm_aperture* h_
     if (st != RTM_OK) return st;
     if (!d_vel || !d_dobs || !d_image)
         return (rtm_status)set_error(RTM_ERR_INVALID, "batch arrays are NULL");
-    const int zc_default = auto_zchunk(p->radius, 64, 16, 1 << 20);
     if (zchunk < 0) return (rtm_status)set_error(RTM_ERR_INVALID, "zchunk < 0");
-    const int zc = zchunk > 0 ? zchunk : zc_default;
-    Plan P = make_plan(p, nshots, h_shots, budget_bytes, zc_default);
-    if (zc != zc_default) {
-        // the workspace was sized with the default slab height; only the
-        // tile counts change with zchunk
-        for (auto& b : P.shots) {
-            b.tiles_z = (b.NZ + zc - 1) / zc;
-            b.ntiles = b.tiles_x * b.tiles_y * b.tiles_z;
-        }
-    }
+    Plan P = make_plan(p, nshots, h_shots, budget_bytes, kBatchZchunk);
     if (!d_ws || ((uintptr_t)d_ws % kAlB))
         return (rtm_status)set_error(RTM_ERR_WORKSPACE, "workspace NULL or not 256-byte aligned");
     if (ws_bytes < P.total)
@@ -213,10 +234,22 @@ rtm_status rtm_batch(const rtm_params* p, int32_t nshots, const rtm_aperture* h_
     int dev = 0, nsm = 0;
     CUB(cudaGetDevice(&dev));
     CUB(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const int bps = batch_blocks_per_sm(p->radius);
+    const bool tma = batch_uses_tma(p->radius);
+    const int bps = tma ? batch_tma_blocks_per_sm(p->radius) : batch_blocks_per_sm(p->radius);
     if (bps < 1) return (rtm_status)set_error(RTM_ERR_CUDA, "batch kernel does not fit on an SM");
     int clock_khz = 0;
     CUB(cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev));
+    // slab height per wave (only the tile counts depend on it)
+    std::vector<int> wave_zc;
+    for (auto& w : P.waves) {
+        const int zc = zchunk > 0 ? zchunk : wave_zchunk(P.shots, w.first, w.second, nsm * bps);
+        wave_zc.push_back(zc);
+        for (int i = w.first; i < w.second; i++) {
+            BatchShot& b = P.shots[i];
+            b.tiles_z = (b.NZ + zc - 1) / zc;
+            b.ntiles = b.tiles_x * b.tiles_y * b.tiles_z;
+        }
+    }
 
     // per-wave buffer pointers and descriptors (all waves share the pool)
     for (auto& w : P.waves) {
@@ -232,17 +265,19 @@ rtm_status rtm_batch(const rtm_params* p, int32_t nshots, const rtm_aperture* h_
                 q += upb(bytes);
                 return reinterpret_cast<float*>(r);
             };
-            b.c = take(4 * N);
             b.gx = take(4 * (size_t)b.NX);
             b.gy = take(4 * (size_t)b.NY);
             b.gz = take(4 * (size_t)b.NZ);
-            b.f0 = take(4 * N);
-            b.f1 = take(4 * N);
-            b.m0 = take(4 * N);
-            b.m1 = take(4 * N);
-            b.ckpt = take(4 * N * 2 * (size_t)(nseg > 1 ? nseg - 1 : 0));
-            b.snap = take(4 * slab * (size_t)p->ckpt_every);
-            b.img = take(4 * slab);
+            b.fstride = (long long)(upb(4 * N) / 4);
+            b.c = take(upb(4 * N) * (5 + 2 * (size_t)(nseg > 1 ? nseg - 1 : 0)));
+            b.f0 = const_cast<float*>(b.c) + 1 * b.fstride;
+            b.f1 = const_cast<float*>(b.c) + 2 * b.fstride;
+            b.m0 = const_cast<float*>(b.c) + 3 * b.fstride;
+            b.m1 = const_cast<float*>(b.c) + 4 * b.fstride;
+            b.ckpt = const_cast<float*>(b.c) + 5 * b.fstride;
+            b.sstride = (long long)(upb(4 * slab) / 4);
+            b.snap = take(upb(4 * slab) * ((size_t)p->ckpt_every + 1));
+            b.img = b.snap + (size_t)p->ckpt_every * b.sstride;
             b.dobs = d_dobs + P.data_off[i];
             b.data = d_data ? d_data + P.data_off[i] : nullptr;
             b.item_base = base;
@@ -260,6 +295,7 @@ rtm_status rtm_batch(const rtm_params* p, int32_t nshots, const rtm_aperture* h_
 
     BatchArgs A;
     memset(&A, 0, sizeof A);
+    std::unique_ptr<BatchTmaArgs> T(tma ? new BatchTmaArgs() : nullptr);
     double a[kMaxRadius + 1];
     weights_b(p->radius, a);
     const double inv_dx2 = 1.0 / (p->dx * p->dx);
@@ -270,7 +306,6 @@ rtm_status rtm_batch(const rtm_params* p, int32_t nshots, const rtm_aperture* h_
     A.nphases = (int)P.phases.size();
     A.ctrl = reinterpret_cast<BatchCtrl*>(ws + P.off_ctrl);
     A.wavelet = reinterpret_cast<const float*>(ws + P.off_wav);
-    A.zchunk = zc;
     A.ckpt_every = p->ckpt_every;
     A.image_every = p->image_every;
     A.nt = p->nt;
@@ -293,7 +328,9 @@ rtm_status rtm_batch(const rtm_params* p, int32_t nshots, const rtm_aperture* h_
     const cudaStream_t s_caller = s;
     s = cs;
     cudaError_t err = cudaSuccess;
-    for (auto& w : P.waves) {
+    for (size_t wi = 0; wi < P.waves.size(); wi++) {
+        const auto& w = P.waves[wi];
+        A.zchunk = wave_zc[wi];
         long long items = 0;
         for (int i = w.first; i < w.second && err == cudaSuccess; i++) {
             const BatchShot& b = P.shots[i];
@@ -311,7 +348,18 @@ rtm_status rtm_batch(const rtm_params* p, int32_t nshots, const rtm_aperture* h_
         A.shots = reinterpret_cast<const BatchShot*>(ws + P.off_desc) + w.first;
         A.nshots = w.second - w.first;
         A.items_per_phase = items;
-        err = launch_batch(p->radius, A, nsm * bps, s);
+        if (tma) {
+            // the launch arguments carry each shot's tensor maps
+            T->a = A;
+            const int nseg = (p->nt + p->ckpt_every - 1) / p->ckpt_every;
+            const int nfields = 5 + 2 * (nseg > 1 ? nseg - 1 : 0);
+            for (int i = w.first; i < w.second && err == cudaSuccess; i++)
+                err = batch_tma_maps(p->radius, P.shots[i], nfields, p->ckpt_every + 1,
+                                     T->maps[i - w.first]);
+            if (err == cudaSuccess) err = launch_batch_tma(p->radius, *T, nsm * bps, s);
+        } else {
+            err = launch_batch(p->radius, A, nsm * bps, s);
+        }
         for (int i = w.first; i < w.second && err == cudaSuccess; i++)
             err = launch_batch_image_add(P.shots[i], p->nx, p->ny, h_shots[i].ox, h_shots[i].oy,
                                          h_shots[i].oz, d_image, s);

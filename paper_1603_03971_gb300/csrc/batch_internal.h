@@ -1,6 +1,7 @@
 // Internal declarations of the batched multi-shot RTM kernel.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -17,11 +18,16 @@ struct BatchShot {
     int src_x, src_y, src_z;  // padded coordinates
     int rec_z;                // padded z of the receiver plane (every model x, y)
     long long item_base;      // first tile of this shot within one phase step
+    // padded fields, fstride floats apart: c, f0, f1, m0, m1, then the
+    // (nseg - 1) checkpoints of two fields (field 5 + 2 (j - 1) + w)
+    long long fstride;
     const float* c;
     float *f0, *f1, *m0, *m1;  // forward and backward field pairs
-    float* ckpt;               // (nseg - 1) checkpoints of two fields
-    float* snap;               // ckpt_every snapshot slabs [nz][ny][NX]
-    float* img;                // image slab
+    float* ckpt;               // checkpoint j, field w: ckpt + (2 (j - 1) + w) fstride
+    // slabs [nz][ny][NX], sstride floats apart: ckpt_every snapshots, then the image
+    long long sstride;
+    float* snap;
+    float* img;                // snap + ckpt_every sstride
     const float *gx, *gy, *gz;
     const float* dobs;         // [nt][ny][nx] data injected backward
     float* data;               // [nt][ny][nx] modelled data, or NULL
@@ -61,6 +67,19 @@ struct BatchArgs {
 };
 
 cudaError_t launch_batch(int radius, const BatchArgs& a, int grid, cudaStream_t s);
+
+// the TMA form (batch_tma.cu): the launch arguments plus three tensor maps
+// per shot of the wave (halo tile and plain tile over the field stack, plain
+// tile over the slab stack)
+struct BatchTmaArgs {
+    BatchArgs a;
+    CUtensorMap maps[kMaxBatchShots][3];
+};
+int batch_tma_tile_x(int radius);
+int batch_tma_blocks_per_sm(int radius);
+cudaError_t batch_tma_maps(int radius, const BatchShot& b, int nfields, int nslabs,
+                           CUtensorMap* maps);
+cudaError_t launch_batch_tma(int radius, const BatchTmaArgs& a, int grid, cudaStream_t s);
 int batch_blocks_per_sm(int radius);
 cudaError_t launch_batch_prep(const BatchShot& sh, const float* vel_full, int full_nx, int full_ny,
                               int ox, int oy, int oz, double dt, float* c, float* gx, float* gy,

@@ -741,6 +741,12 @@ rtm_status common_checks(const rtm_params* p, const float* d_c, const int32_t* d
 
 }  // namespace
 
+int rtm::tuning_variant(int radius) {
+    if (radius < 0 || radius > kMaxRadius) return 0;
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_variant[radius];
+}
+
 int rtm::set_error(int code, const char* fmt, ...) {
     char buf[512];
     va_list ap;

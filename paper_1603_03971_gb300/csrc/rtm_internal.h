@@ -125,5 +125,7 @@ cudaError_t launch_image_laplacian(const float* image, int nx, int ny, int nz,
 
 // sets the thread-local message of rtm_last_error() and returns code
 int set_error(int code, const char* fmt, ...);
+// plane-load variant chosen by rtm_set_tuning for a radius (0: automatic)
+int tuning_variant(int radius);
 
 }  // namespace rtm

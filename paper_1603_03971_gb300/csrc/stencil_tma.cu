@@ -166,13 +166,15 @@ __host__ __device__ constexpr int tma_prefetch() {
 }
 
 // the register queue moves once per G planes (2r + G entries, the plane body
-// unrolled G times): 2r / G vector moves per plane instead of 2r. Radius 8,
-// 576^3: G = 1 / 2 / 4 gave 204.8 / 210.6 / 215.8 Gpoint-updates/s; radius 4
-// (80 registers for three blocks) keeps G = 1
+// unrolled G times): 2r / G vector moves per plane instead of 2r. 576^3,
+// radius 8: G = 1 / 2 / 4 gave 204.8 / 210.6 / 215.8 Gpoint-updates/s;
+// radius 4: G = 1 / 2 gave 318.4 / 320.8 (G = 3 spills under the 80-register
+// cap of three blocks per SM)
 constexpr int kQueueGroup8 = 4;
+constexpr int kQueueGroup4 = 2;
 template <int R>
 __host__ __device__ constexpr int queue_group() {
-    return R == 8 ? kQueueGroup8 : 1;
+    return R == 8 ? kQueueGroup8 : kQueueGroup4;
 }
 
 template <int R, int MODE>

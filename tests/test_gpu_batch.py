@@ -1,6 +1,7 @@
 """Batched multi-shot RTM (one persistent cooperative launch per wave) against
 the FP64 oracle run shot by shot on each aperture, and invariance of the
-result to the wave split and the work-item slab height."""
+result to the wave split and the work-item slab height. Every test runs with
+both batched kernels: TMA plane loads (the default) and vector loads."""
 import ctypes
 
 import numpy as np
@@ -11,6 +12,17 @@ from helpers import rel_l2
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
+
+
+@pytest.fixture(autouse=True, params=[0, 1], ids=["tma", "vector"])
+def kernel_variant(request):
+    import paper_1603_03971_gb300 as rtm
+
+    for r in (4, 8):
+        rtm.set_tuning(r, 0, request.param)
+    yield request.param
+    for r in (4, 8):
+        rtm.set_tuning(r, 0, 0)
 
 FULL = (64, 80, 96)  # nz, ny, nx of the common model
 APERTURES = [  # ox, oy, oz, nx, ny, nz, src (x, y, z), rec_z  (aperture coordinates)
