@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--batch", action="store_true",
                     help="also run the batched-shots leg (32 apertures, radius 8)")
     ap.add_argument("--batch-nt", type=int, default=1500)
+    ap.add_argument("--batch-shots", default="all",
+                    help="comma-separated aperture indices of the batched workload (default all 32)")
+    ap.add_argument("--batch-ckpt", type=int, default=50, help="checkpoint interval of the batch")
     ap.add_argument("--imaging", action="store_true",
                     help="also time the imaging-condition variants (source illumination, "
                          "normalised and Laplacian-filtered image) on the main workload")
@@ -500,9 +503,12 @@ def batch_leg(args, dev):
     origin, size = rtm_inputs.batch_apertures(cfg["nshots"], (nz, ny, nx), seed=cfg["seed"])
     aps = [B.Aperture(int(o[0]), int(o[1]), int(o[2]), int(s[0]), int(s[1]), int(s[2]),
                       int(s[0]) // 2, int(s[1]) // 2, 4, 2) for o, s in zip(origin, size)]
+    if args.batch_shots != "all":  # a subset of the seeded apertures (profiling)
+        aps = [aps[int(i)] for i in args.batch_shots.split(",")]
     dt = rtm_inputs.courant_dt(cfg["dx"], cfg["vmax"])
     p = rtm.make_params(nx, ny, nz, cfg["nb"], cfg["radius"], nt, cfg["dx"], dt, cfg["f0"],
-                        1.0 / cfg["f0"], (0, 0, 0), 0, storage="ckpt", ckpt_every=50)
+                        1.0 / cfg["f0"], (0, 0, 0), 0, storage="ckpt",
+                        ckpt_every=args.batch_ckpt)
     budget = 200 * 10 ** 9
     ws = B.alloc_workspace(p, aps, budget, device=dev)
     dobs = torch.zeros(B.data_size(p, aps), dtype=torch.float32, device=dev)
@@ -518,8 +524,11 @@ def batch_leg(args, dev):
     rtm.check(ws)
     pts = sum((a.nx + 2 * p.nb) * (a.ny + 2 * p.nb) * (a.nz + 2 * p.nb) for a in aps)
     updates = 3 * nt * pts
-    return {"workload": "32 shots, apertures 128-384 x 128-384 x 256-512 of a 1024x1024x512 "
-                        "layered/salt model, r=8, %d steps, checkpoint every 50" % nt,
+    shots = ("32 shots" if args.batch_shots == "all"
+             else "shots %s of the 32" % args.batch_shots)
+    return {"workload": "%s, apertures 128-384 x 128-384 x 256-512 of a 1024x1024x512 "
+                        "layered/salt model, r=8, %d steps, checkpoint every %d"
+                        % (shots, nt, args.batch_ckpt),
             "seconds": t, "gpoint_updates_per_s": updates / t / 1e9, "updates": updates,
             "workspace_gb": ws.numel() / 1e9}
 

@@ -1075,16 +1075,32 @@ rtm_status rtm_shot_host(const rtm_params* p, const float* h_vel, int32_t vel_ki
     float* dobs = reinterpret_cast<float*>(base + off);
     off += up(sizeof(float) * (size_t)p->nt * p->nrec);
     float* img = reinterpret_cast<float*>(base + off);
+    // the observed data are read only by the receiver pass: they travel on a
+    // side stream while the model is prepared and the source is propagated
+    struct Side {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        ~Side() {
+            if (st) cudaStreamSynchronize(st);
+            if (ev) cudaEventDestroy(ev);
+            if (st) cudaStreamDestroy(st);
+        }
+    } side;
+    CU(cudaStreamCreateWithFlags(&side.st, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&side.ev, cudaEventDisableTiming));
+    if (p->nrec > 0)
+        CU(cudaMemcpyAsync(dobs, h_dobs, sizeof(float) * (size_t)p->nt * p->nrec,
+                           cudaMemcpyHostToDevice, side.st));
+    CU(cudaEventRecord(side.ev, side.st));
     CU(cudaMemcpyAsync(vel, h_vel, sizeof(float) * d.nmodel, cudaMemcpyHostToDevice, s));
-    if (p->nrec > 0) {
+    if (p->nrec > 0)
         CU(cudaMemcpyAsync(rec, h_rec, sizeof(int32_t) * 3 * (size_t)p->nrec,
                            cudaMemcpyHostToDevice, s));
-        CU(cudaMemcpyAsync(dobs, h_dobs, sizeof(float) * (size_t)p->nt * p->nrec,
-                           cudaMemcpyHostToDevice, s));
-    }
     CHECK(rtm_model_prep(p, vel, vel_kind, c, d_ws, ws_bytes, stream));
     CU(cudaMemsetAsync(img, 0, sizeof(float) * d.nmodel, s));
-    CHECK(rtm_shot(p, c, rec, dobs, nullptr, d_ws, ws_bytes, img, stream));
+    CHECK(rtm_forward(p, c, rec, nullptr, d_ws, ws_bytes, nullptr, stream));
+    CU(cudaStreamWaitEvent(s, side.ev, 0));
+    CHECK(rtm_backward_image(p, c, rec, dobs, d_ws, ws_bytes, img, nullptr, stream));
     CU(cudaMemcpyAsync(h_image, img, sizeof(float) * d.nmodel, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     return RTM_OK;
