@@ -18,13 +18,18 @@
 //
 // Roles: warp 8 (one thread) issues the TMA plane loads (up to kLook planes
 // ahead) and the MMAs into one of two accumulator buffers (2 x 256 columns);
-// warpgroup 0 finishes even planes, warpgroup 1 odd planes: tcgen05.ld of the
-// 8 parity accumulators of its row, LeakyReLU(acc + b3) rounded to bfloat16
-// (as the training decoder rounds g1), D2 on the CUDA cores and the 4 x 4 x 4
-// output block of the latent voxel stored as float4 rows, scaled by the
-// snapshot's rms. mbarriers: plane full (TMA bytes), plane free (commit of
-// the last MMAs that read it), accumulator full (commit), accumulator free
-// (128 epilogue arrivals). Every wait is bounded and shares an abort flag.
+// warpgroup 0 finishes even planes, warpgroup 1 odd planes, four parities at
+// a time: tcgen05.ld of their accumulators (one row per thread),
+// LeakyReLU(acc + b3) rounded to bfloat16 (as the training decoder rounds
+// g1) into four 128 x 32 K-major A operands in shared memory, then one
+// thread issues D2 as tensor-core products, [128 x 32] g1 x [32 x 16] W4
+// (rows 8..15 zero), into the accumulator columns just drained; the 8 results
+// per parity are read back, scaled by the snapshot's rms and stored as the
+// float4 rows of the latent voxel's 4 x 4 x 4 output block. mbarriers: plane
+// full (TMA bytes), plane free (commit of the last MMAs that read it),
+// accumulator full (commit), accumulator free (128 epilogue arrivals), D2
+// done (commit). Every wait is bounded and shares an abort flag; the
+// warpgroups vote on each wait's outcome, so they leave together.
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -48,7 +53,10 @@ constexpr int kTmaBytes = 2 * HX * HY * 16;    // bytes one plane load delivers
 constexpr int kSlots = 9;                      // plane ring
 constexpr int kLook = kSlots - 4;              // planes loaded beyond the newest one needed
 constexpr int kW3Bytes = 64 * 1024;            // 64 B operands (parity, tap): 32 x 16, 1 KB each
-constexpr int kSmem = 128 + kW3Bytes + kSlots * kPlaneBytes + 288 * 4;  // > half an SM: 1 CTA
+constexpr int kA2Bytes = 128 * 32 * 2;          // D2 A operand: 128 rows x 32 channels, bf16
+// W3 operands, plane ring, b3 (128 B), the D2 B operand W4 (16 x 32 bf16,
+// 1 KB), four D2 A operands per epilogue warpgroup: > half an SM, 1 CTA
+constexpr int kSmem = 128 + kW3Bytes + kSlots * kPlaneBytes + 128 + 1024 + 2 * 4 * kA2Bytes;
 constexpr int kTmemCols = 512;
 constexpr int kThreads = 288;
 constexpr long long kLimit = 1LL << 24;
@@ -79,7 +87,6 @@ __device__ __forceinline__ void taps(int q, int tau, int& t, int& k) {
 }
 
 __device__ __forceinline__ float lrelu(float a) { return a > 0.f ? a : kSlope * a; }
-__device__ __forceinline__ float rbf(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
 
 __device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(b)),
@@ -129,6 +136,31 @@ __device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, float* out) {
 #pragma unroll
     for (int i = 0; i < 16; i++) out[i] = __uint_as_float(r[i]);
 }
+// all 128 threads of a warpgroup (named barrier id) agree: true only if v is
+// true in every one of them; also a barrier of the warpgroup
+__device__ __forceinline__ bool wg_all(bool v, int id) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id)
+        : "memory");
+    return r != 0;
+}
+// 8 columns of this warp's lanes, without waiting
+__device__ __forceinline__ void tmem_ld8_nw(uint32_t taddr, float* out) {
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; i++) out[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -142,7 +174,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_decode_march(const __grid_constant__ D12Args A, const __grid_constant__ CUtensorMap map,
                    const Sched S, int* status) {
     extern __shared__ uint8_t dsm_raw[];
-    __shared__ __align__(8) uint64_t full[kSlots], freed[kSlots], acc_full[2], acc_free[2], fin;
+    __shared__ __align__(8) uint64_t full[kSlots], freed[kSlots], acc_full[2], acc_free[2], fin,
+        d2_full[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -150,7 +183,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         (reinterpret_cast<uintptr_t>(dsm_raw) + 127) & ~static_cast<uintptr_t>(127));
     uint8_t* w3 = base;
     uint8_t* ring = base + kW3Bytes;
-    float* w4 = reinterpret_cast<float*>(ring + kSlots * kPlaneBytes);  // [8][32], then b3[32]
+    float* b3s = reinterpret_cast<float*>(ring + kSlots * kPlaneBytes);  // b3[32]
+    uint8_t* b4t = ring + kSlots * kPlaneBytes + 128;  // W4 as a 16 x 32 K-major operand
+    uint8_t* a2 = b4t + 1024;                          // D2 A operands
 
     const D1Args& d = A.d1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -164,6 +199,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int b = 0; b < 2; b++) {
             tc::mbar_init(&acc_full[b], 1);
             tc::mbar_init(&acc_free[b], 128);
+            tc::mbar_init(&d2_full[b], 1);
         }
         tc::mbar_init(&fin, 1);
         abort_flag = 0;
@@ -183,8 +219,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int e = 0; e < 8; e++) w[e] = d.P[kOW3 + o * 1024 + ktap * 16 + 8 * j + e];
         *reinterpret_cast<uint4*>(w3 + t * 1024 + b_off(o, 8 * j)) = tc::pack8(w);
     }
-    for (int i = tid; i < 256; i += kThreads) w4[i] = rbf(d.P[kOW4 + i]);
-    if (tid < 32) w4[256 + tid] = d.P[kOB3 + tid];
+    // W4[e][c] (e = (ez, ey, ex), c = channel) as rows e of a 16 x 32 K-major
+    // bf16 operand, rows 8..15 zero
+    for (int idx = tid; idx < 16 * 4; idx += kThreads) {
+        const int e = idx >> 2, c8 = (idx & 3) * 8;
+        float w[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) w[i] = e < 8 ? d.P[kOW4 + e * 32 + c8 + i] : 0.f;
+        tc::st_vec8(b4t, e, c8, tc::pack8(w));
+    }
+    if (tid < 32) b3s[tid] = d.P[kOB3 + tid];
     tc::fence_proxy_async();
     tc::tc_fence_before();
     __syncthreads();
@@ -288,9 +332,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float sc = A.sigma ? *A.sigma : 1.0f;
         const bool vec = ((reinterpret_cast<uintptr_t>(A.out.p) & 15) == 0) &&
                          (A.out.sy % 4 == 0) && (A.out.sz % 4 == 0);
-        const float4* w4v = reinterpret_cast<const float4*>(w4);
-        int out = 0;
-        bool ok = true;
+        const float4* b3v = reinterpret_cast<const float4*>(b3s);
+        uint8_t* atile = a2 + g * 4 * kA2Bytes;  // this warpgroup's four D2 A operands
+        constexpr uint32_t idesc2 = tc::idesc_bf16(128, 16);
+        int out = 0, d2_phase = 0;
+        bool ok = true, d2_pending = false;
         for (int item = blockIdx.x; item < S.nitems && ok; item += gridDim.x) {
             int cx, cy, z0, nz;
             item_coords(S, lnz, item, cx, cy, z0, nz);
@@ -299,68 +345,106 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int zi = 0; zi < nz; zi++, out++) {
                 if ((out & 1) != g) continue;
                 const int u = out >> 1;
-                ok = wait_bar(&acc_full[g], (uint32_t)(u & 1), abrt);
+                ok = wg_all(wait_bar(&acc_full[g], (uint32_t)(u & 1), abrt), 1 + g);
                 if (!ok) break;
                 tc::tc_fence_after();
                 const int Z = z0 + zi;
                 const uint32_t tb = lane_base + g * 256;
 #pragma unroll 1
-                for (int qzy = 0; qzy < 4; qzy++) {
-                    const int qz = qzy >> 1, qy = qzy & 1;
-                    float a0[32], a1[32];
-                    tmem_ld16_nw(tb + (qzy * 2) * 32, a0);
-                    tmem_ld16_nw(tb + (qzy * 2) * 32 + 16, a0 + 16);
-                    tmem_ld16_nw(tb + (qzy * 2 + 1) * 32, a1);
-                    tmem_ld16_nw(tb + (qzy * 2 + 1) * 32 + 16, a1 + 16);
-                    tmem_wait_ld();
-                    if (!valid) continue;
-#pragma unroll
-                    for (int c4 = 0; c4 < 8; c4++) {
-                        const float4 bb = w4v[64 + c4];
-                        const float b_[4] = {bb.x, bb.y, bb.z, bb.w};
-#pragma unroll
-                        for (int i = 0; i < 4; i++) {
-                            a0[4 * c4 + i] = rbf(lrelu(a0[4 * c4 + i] + b_[i]));
-                            a1[4 * c4 + i] = rbf(lrelu(a1[4 * c4 + i] + b_[i]));
-                        }
-                    }
+                for (int qz = 0; qz < 2 && ok; qz++) {
+                    // g1 = bf16(LeakyReLU(acc + b3)) of the four parities (qz, qy, qx)
+                    // into the A operands (row = latent voxel, K = channel)
 #pragma unroll 1
-                    for (int ezy = 0; ezy < 4; ezy++) {
-                        const int e0 = ezy * 2;  // ex = 0; e0 + 1: ex = 1
-                        float y00 = 0.f, y01 = 0.f, y10 = 0.f, y11 = 0.f;
+                    for (int qy = 0; qy < 2; qy++) {
+                        const int qzy = qz * 2 + qy;
+                        float a0[32], a1[32];
+                        tmem_ld16_nw(tb + (qzy * 2) * 32, a0);
+                        tmem_ld16_nw(tb + (qzy * 2) * 32 + 16, a0 + 16);
+                        tmem_ld16_nw(tb + (qzy * 2 + 1) * 32, a1);
+                        tmem_ld16_nw(tb + (qzy * 2 + 1) * 32 + 16, a1 + 16);
+                        tmem_wait_ld();
 #pragma unroll
                         for (int c4 = 0; c4 < 8; c4++) {
-                            const float4 wa = w4v[e0 * 8 + c4], wb = w4v[(e0 + 1) * 8 + c4];
-                            const float wa_[4] = {wa.x, wa.y, wa.z, wa.w};
-                            const float wb_[4] = {wb.x, wb.y, wb.z, wb.w};
+                            const float4 bb = b3v[c4];
+                            const float b_[4] = {bb.x, bb.y, bb.z, bb.w};
 #pragma unroll
                             for (int i = 0; i < 4; i++) {
-                                const int c = 4 * c4 + i;
-                                y00 = fmaf(wa_[i], a0[c], y00);
-                                y01 = fmaf(wb_[i], a0[c], y01);
-                                y10 = fmaf(wa_[i], a1[c], y10);
-                                y11 = fmaf(wb_[i], a1[c], y11);
+                                a0[4 * c4 + i] = lrelu(a0[4 * c4 + i] + b_[i]);
+                                a1[4 * c4 + i] = lrelu(a1[4 * c4 + i] + b_[i]);
                             }
                         }
-                        const int ez = ezy >> 1, ey = ezy & 1;
-                        float* o = A.out.p + (long long)(4 * Z + 2 * qz + ez) * A.out.sz +
-                                   (long long)(4 * Y + 2 * qy + ey) * A.out.sy + 4 * X;
-                        const float4 v = make_float4(sc * (y00 + b4), sc * (y01 + b4),
-                                                     sc * (y10 + b4), sc * (y11 + b4));
-                        if (vec) {
-                            *reinterpret_cast<float4*>(o) = v;
-                        } else {
-                            o[0] = v.x;
-                            o[1] = v.y;
-                            o[2] = v.z;
-                            o[3] = v.w;
+                        uint8_t* t0 = atile + (qy * 2) * kA2Bytes;
+                        uint8_t* t1 = t0 + kA2Bytes;
+#pragma unroll
+                        for (int k8 = 0; k8 < 4; k8++) {
+                            tc::st_vec8(t0, row, 8 * k8, tc::pack8(a0 + 8 * k8));
+                            tc::st_vec8(t1, row, 8 * k8, tc::pack8(a1 + 8 * k8));
+                        }
+                    }
+                    // the generic-proxy tile writes and the drained accumulator
+                    // columns, then one thread issues the D2 products into those
+                    // columns: [128 x 32] g1 x [32 x 16] W4 (rows 8..15 zero)
+                    tc::fence_proxy_async();
+                    tc::tc_fence_before();
+                    asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
+                    if (row == 0) {
+                        tc::tc_fence_after();
+                        const uint64_t dB = tc::sdesc(tc::smem_u32(b4t), 128, 512);
+#pragma unroll
+                        for (int p = 0; p < 4; p++) {
+                            const uint64_t dA =
+                                tc::sdesc(tc::smem_u32(atile + p * kA2Bytes), 128, 512);
+                            const uint32_t dcol = tmem + g * 256 + (qz * 4 + p) * 32;
+                            tc::mma_bf16(dcol, dA, dB, idesc2, 0u);
+                            tc::mma_bf16(dcol, dA + 16, dB + 16, idesc2, 1u);  // K 16..31
+                        }
+                        tc::mma_commit(&d2_full[g]);
+                        d2_pending = true;
+                    }
+                    // (the vote also orders the next half's tile writes after
+                    // every thread's wait: the products have read the tiles)
+                    ok = wg_all(wait_bar(&d2_full[g], (uint32_t)(d2_phase & 1), abrt), 1 + g);
+                    if (!ok) break;
+                    d2_phase++;
+                    if (row == 0) d2_pending = false;
+                    tc::tc_fence_after();
+                    float y[4][8];
+#pragma unroll
+                    for (int p = 0; p < 4; p++) tmem_ld8_nw(tb + (qz * 4 + p) * 32, y[p]);
+                    tmem_wait_ld();
+                    if (valid) {
+#pragma unroll
+                        for (int qy = 0; qy < 2; qy++) {
+#pragma unroll
+                            for (int ezy = 0; ezy < 4; ezy++) {
+                                const int ez = ezy >> 1, ey = ezy & 1;
+                                // x: (qx, ex) = (0, 0), (0, 1), (1, 0), (1, 1)
+                                const float* ya = y[qy * 2];
+                                const float* yb = y[qy * 2 + 1];
+                                float* o = A.out.p + (long long)(4 * Z + 2 * qz + ez) * A.out.sz +
+                                           (long long)(4 * Y + 2 * qy + ey) * A.out.sy + 4 * X;
+                                const float4 v = make_float4(
+                                    sc * (ya[ezy * 2] + b4), sc * (ya[ezy * 2 + 1] + b4),
+                                    sc * (yb[ezy * 2] + b4), sc * (yb[ezy * 2 + 1] + b4));
+                                if (vec) {
+                                    *reinterpret_cast<float4*>(o) = v;
+                                } else {
+                                    o[0] = v.x;
+                                    o[1] = v.y;
+                                    o[2] = v.z;
+                                    o[3] = v.w;
+                                }
+                            }
                         }
                     }
                 }
+                if (!ok) break;
                 tc::tc_fence_before();
                 bar_arrive(&acc_free[g]);
             }
         }
+        // products still in flight must complete before the tensor memory is freed
+        if (d2_pending) wait_bar(&d2_full[g], (uint32_t)(d2_phase & 1), nullptr);
     }
     tc::tc_fence_before();
     __syncthreads();

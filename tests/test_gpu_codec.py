@@ -110,9 +110,12 @@ def test_strided_snapshot_views_encode_identically():
 def test_marching_decoder_equals_gemm_decoder(shape):
     """The z-marching decoder (TMA plane loads read in place by the tensor
     cores, several z chunks and ragged x / y columns at the largest shape)
-    and the GEMM-engine decoder form the same sums in the same order: equal
-    outputs, into dense arrays and into strided views whose rows are not
-    16-byte aligned."""
+    and the GEMM-engine decoder: the same bfloat16 g1 and weights, D1 summed
+    in the same order; D2's 32 products are exact in float32 and summed by
+    the tensor cores in the marching decoder, sequentially in the other, so
+    the outputs agree to float32 rounding of a 32-term sum. The strided
+    output (rows not 16-byte aligned) equals the dense one exactly and leaves
+    the columns beside it untouched."""
     import torch
 
     from paper_1603_03971_gb300 import codec
@@ -136,8 +139,11 @@ def test_marching_decoder_equals_gemm_decoder(shape):
     import paper_1603_03971_gb300 as rtm
 
     rtm.check(ws)
-    assert torch.equal(out, ref)
-    assert torch.equal(big[:, :, 1:1 + nx], ref)
+    scale = float(ref.abs().max())
+    assert scale > 0
+    assert float((out - ref).abs().max()) <= 2e-6 * scale
+    assert rel_l2(out.cpu().numpy(), ref.cpu().numpy()) <= 1e-6
+    assert torch.equal(big[:, :, 1:1 + nx], out)
     assert bool(big[:, :, 0].isnan().all()) and bool(big[:, :, 1 + nx:].isnan().all())
 
 
