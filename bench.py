@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--learned-window", type=int, default=200,
                     help="exact window: the first steps whose snapshots are recomputed from the "
                          "zero state instead of coded (checkpoint-recompute fallback)")
+    ap.add_argument("--no-grad", action="store_true",
+                    help="skip the velocity-gradient leg (gradient_256 workload)")
     ap.add_argument("--no-boundary", action="store_true",
                     help="skip the boundary-storage shot (reverse time stepping)")
     ap.add_argument("--batch", action="store_true",
@@ -486,6 +488,57 @@ def boundary_leg(w, vel, rec, dobs, dev, ref_image, ref_shot_s, ref_ws_gb):
     return res
 
 
+def grad_leg(dev):
+    """The velocity gradient of the data misfit on the gradient_256 workload
+    (256^3 smooth random model, 320^3 padded, 1000 steps, checkpoints every
+    25): the forward pass (data + checkpoints), then rtm_grad (segment
+    recompute writing L u, receiver propagation of the residual correlating
+    it). CUDA events around both; per-mode bandwidth from the statistics."""
+    import torch
+
+    import paper_1603_03971_gb300 as rtm
+    import rtm_inputs
+
+    w = rtm_inputs.WORKLOADS["gradient_256"]
+    p = rtm.params_for(w, want_grad=True)
+    ws = rtm.alloc_workspace(p, dev)
+    c = rtm.model_prep(p, w.velocity_model(device=dev).contiguous(), ws)
+    rec = torch.from_numpy(w.receivers()).to(dev)
+    d = torch.empty((w.nt, p.nrec), dtype=torch.float32, device=dev)
+    rtm.forward(p, c, rec, ws, data=d)
+    resid = 1e-2 * d  # any residual times the same kernels
+    rtm.grad(p, c, rec, resid, ws)  # warm-up
+    rtm.forward(p, c, rec, ws, data=d)
+    torch.cuda.synchronize()
+    rtm.reset_stats()
+    rtm.set_timing(True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    rtm.forward(p, c, rec, ws, data=d)
+    ev[1].record()
+    g = rtm.grad(p, c, rec, resid, ws)
+    ev[2].record()
+    torch.cuda.synchronize()
+    rtm.set_timing(False)
+    st = rtm.stats()
+    rtm.check(ws)
+    t_f = ev[0].elapsed_time(ev[1]) / 1e3
+    t_g = ev[1].elapsed_time(ev[2]) / 1e3
+    NZ, NY, NX = w.padded_shape
+    updates = 3 * w.nt * NX * NY * NZ
+    hbm, _ = measured_peaks()
+    modes = {k: {"ms_per_launch": v["ms"] / v["launches"], "gbs": v["bytes"] / v["ms"] / 1e6,
+                 "frac": v["bytes"] / v["ms"] / 1e6 / hbm}
+             for k, v in st["stencil"].items() if v["launches"] and v["ms"] > 0}
+    res = {"workload": "gradient_256: 256^3 smooth random model (320^3 padded), r=4, %d steps, "
+                       "checkpoint every %d" % (w.nt, w.ckpt_every),
+           "forward_s": t_f, "gradient_s": t_g,
+           "gpoint_updates_per_s": updates / (t_f + t_g) / 1e9,
+           "gradient_finite": bool(torch.isfinite(g).all()), "stencil_modes": modes}
+    del ws
+    return res
+
+
 def batch_leg(args, dev):
     """32 shots on seeded uneven apertures of a 1024 x 1024 x 512 layered /
     salt model, radius-8 stencil, each a full checkpointed RTM, in one
@@ -650,6 +703,9 @@ def run_ours(args):
     imaging_res = None
     if rank == 0 and args.imaging:
         imaging_res = imaging_leg(p, c, rec, dobs, ws, dev)
+    grad_res = None
+    if rank == 0 and not args.no_grad:
+        grad_res = grad_leg(dev)
     boundary_res = None
     if rank == 0 and not args.no_boundary:
         ref = image / float(args.warmup + args.steps)  # one shot's checkpoint image
@@ -692,6 +748,7 @@ def run_ours(args):
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": st["launches"],
             "clocks": clocks, "impl": "ours", "learned": learned, "batch": batch_res,
             "imaging": imaging_res, "revolve": revolve_res, "boundary": boundary_res,
+            "gradient": grad_res,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
