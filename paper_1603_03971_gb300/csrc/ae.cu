@@ -941,8 +941,16 @@ cudaError_t ae_rms(const Vol& in, AeScalars* sc, cudaStream_t s) {
 }
 
 cudaError_t ae_encode(const float* P, const Vol& in, bf16* h1, bf16* lat, AeScalars* sc,
-                      float* sigma_out, int* status, cudaStream_t s, bool keep_h1) {
-    cudaError_t e = ae_rms(in, sc, s);
+                      float* sigma_out, int* status, cudaStream_t s, bool keep_h1,
+                      bool sumsq_ready) {
+    cudaError_t e = cudaSuccess;
+    if (sumsq_ready) {
+        k_scale<<<1, 1, 0, s>>>(&sc->sumsq, (long long)in.nx * in.ny * in.nz, &sc->sigma,
+                                &sc->inv_sigma);
+        e = cudaGetLastError();
+    } else {
+        e = ae_rms(in, sc, s);
+    }
     if (e != cudaSuccess) return e;
     const Dims3 h{in.nx / 2, in.ny / 2, in.nz / 2}, l{in.nx / 4, in.ny / 4, in.nz / 4};
     e = keep_h1 ? cudaErrorNotSupported : ae_encode_march(P, in, &sc->inv_sigma, lat, status, s);

@@ -64,10 +64,12 @@ cudaError_t ae_rms(const ae::Vol& in, ae::AeScalars* sc, cudaStream_t s);
 // snapshot -> latent; the snapshot's rms goes to sigma_out if given. With
 // keep_h1 the GEMM-engine layers run and leave E1's output in h1 (training
 // reads it); otherwise the z-marching kernel runs where it can and h1 is
-// untouched scratch.
+// untouched scratch. With sumsq_ready, sc->sumsq already holds the
+// snapshot's sum of squares (accumulated by the stencil step that wrote it)
+// and only the scale is derived from it.
 cudaError_t ae_encode(const float* P, const ae::Vol& in, ae::bf16* h1, ae::bf16* lat,
                       ae::AeScalars* sc, float* sigma_out, int* status, cudaStream_t s,
-                      bool keep_h1 = false);
+                      bool keep_h1 = false, bool sumsq_ready = false);
 // latent -> snapshot scaled by *sigma (1 if NULL); with g1 NULL the two
 // decoder layers run fused (inference), otherwise g1 keeps the D1 output
 cudaError_t ae_decode(const float* P, const ae::bf16* lat, const float* sigma, const ae::Vol& out,

@@ -395,12 +395,16 @@ double stencil_bytes(const Ctx& C, int mode) {
     }
 }
 
-rtm_status stencil(Ctx& C, int mode, const float* cur, float* prev, float* snap, float* acc) {
+rtm_status stencil(Ctx& C, int mode, const float* cur, float* prev, float* snap, float* acc,
+                   double* sumsq = nullptr) {
     StepArgs a = C.base;
     a.u_cur = cur;
     a.u_prev = prev;
     a.snap = snap;
     a.acc = acc;
+    a.sumsq = sumsq;
+    // the statistics count the sum-of-squares forward step as a forward step
+    const int slot = mode == MODE_FWD_SUMSQ ? MODE_FWD : mode;
     set_region(a, mode);
     if (mode == MODE_REV && C.zchunk_auto)  // slabs sized for the model region's tiles
         a.zchunk = auto_zchunk(C.p->radius, a.xend - a.xorg, a.yend - a.yorg, a.zend - a.zorg);
@@ -410,10 +414,10 @@ rtm_status stencil(Ctx& C, int mode, const float* cur, float* prev, float* snap,
         std::lock_guard<std::mutex> lk(g_mu);
         timing = g_timing;
         g_stats.launches += 1;
-        g_stats.stencil_launches[mode] += 1;
+        g_stats.stencil_launches[slot] += 1;
     }
     if (timing) {
-        PendingTiming t{t_timer.get(), t_timer.get(), mode, stencil_bytes(C, mode)};
+        PendingTiming t{t_timer.get(), t_timer.get(), slot, stencil_bytes(C, slot)};
         CU(cudaEventRecord(t.a, C.s));
         CU(C.variant == 2 ? launch_stencil_tma(C.p->radius, mode, a, C.status(), C.s)
                           : launch_stencil(C.p->radius, mode, a, C.s));
@@ -482,19 +486,28 @@ rtm_status run_forward(Ctx& C, const int32_t* rec, float* data, float* u_last) {
                 snap = C.snap_slot((size_t)((n + 1) / ie - 1));
             }
         }
-        CHECK(stencil(C, mode, cur, prev, snap, nullptr));
+        // learned storage: the step that writes a coded snapshot also sums
+        // its squares for the encoder's scale (no separate pass over it)
+        const bool code = p->storage == RTM_STORE_LEARNED && (n + 1) % ie == 0 &&
+                          n + 1 > p->ckpt_every;
+        auto* scal = reinterpret_cast<ae::AeScalars*>(C.at(C.L.ae_scalars));
+        if (code) {
+            CU(cudaMemsetAsync(&scal->sumsq, 0, sizeof(double), C.s));
+            mode = MODE_FWD_SUMSQ;
+        }
+        CHECK(stencil(C, mode, cur, prev, snap, nullptr, code ? &scal->sumsq : nullptr));
         if (p->storage == RTM_STORE_BOUNDARY && n + 1 <= p->nt - 2) {
             // the band of u^{n+1} (now in prev)
             CU(launch_band_copy(C.G, p->radius, prev, C.band_of(n + 1), 0, C.s));
             count_launch();
         }
-        if (p->storage == RTM_STORE_LEARNED && (n + 1) % ie == 0 && n + 1 > p->ckpt_every) {
+        if (code) {
             // the encoder reads u^{n+1} (now in prev) in place: no snapshot copy
             const size_t k = (size_t)((n + 1) / ie - 1);
             CU(ae_encode(C.ae, C.field_view(prev), reinterpret_cast<ae::bf16*>(C.at(C.L.ae_h)),
-                         C.latent_slot(k), reinterpret_cast<ae::AeScalars*>(C.at(C.L.ae_scalars)),
-                         C.at(C.L.scales) + k, C.status(), C.s));
-            count_launch(4);
+                         C.latent_slot(k), scal, C.at(C.L.scales) + k, C.status(), C.s,
+                         false, true));
+            count_launch(2);  // scale, encoder
         }
         float* t = prev;
         prev = cur;

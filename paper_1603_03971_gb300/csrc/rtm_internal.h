@@ -20,7 +20,8 @@ enum StencilMode : int {
     MODE_REV = 6,       // reverse step over the model region, sponge factor 1:
                         // u^{n-1} = 2u^n + c L u^n - u^{n+1} (cells outside the
                         // model keep their value)
-    MODE_COUNT = 7
+    MODE_FWD_SUMSQ = 7, // + sum of squares of the new field over the model region (+= *sumsq)
+    MODE_COUNT = 8
 };
 
 constexpr int kMaxRadius = 8;
@@ -46,6 +47,7 @@ struct StepArgs {
     // MODE_REV, which covers the model region
     int xorg, xend, yorg, yend, zorg, zend;
     int snap_padded;     // MODE_BWD_IMAGE: snapshot on the padded grid instead of the slab
+    double* sumsq;       // MODE_FWD_SUMSQ: accumulator of the model region's sum of squares
     float a[kMaxRadius + 1];  // a[0] = 3 a0 / dx^2, a[k] = a_k / dx^2
 };
 

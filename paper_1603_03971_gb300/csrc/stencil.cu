@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(256, R == 4 ? 2 : 1) k_stencil(const __grid_co
     };
     load_epi(zb, e1, e2);
 
+    float ssq = 0.f;  // MODE_FWD_SUMSQ: this thread's share of the sum of squares
     for (int z = zb; z < ze; z++) {
         float(*S)[T::SW] = sm[(z - zb) & 1];
         // stage plane z
@@ -180,7 +181,13 @@ __global__ void __launch_bounds__(256, R == 4 ? 2 : 1) k_stencil(const __grid_co
             const size_t o = (size_t)z * plane + col;
             st_stream(A.u_prev + o, out);
 
-            if constexpr (MODE == MODE_FWD_SNAP) {
+            if constexpr (MODE == MODE_FWD_SUMSQ) {
+                if (ym && z >= A.nb && z < A.nb + A.nz) {
+#pragma unroll
+                    for (int i = 0; i < 4; i++)
+                        if (x + i >= A.nb && x + i < A.nb + A.nx) ssq = fmaf(out.v[i], out.v[i], ssq);
+                }
+            } else if constexpr (MODE == MODE_FWD_SNAP) {
                 if (xm && ym && z >= A.nb && z < A.nb + A.nz)
                     st_stream(A.snap + (size_t)(z - A.nb) * slab_plane + slab_col, out);
             } else if constexpr (MODE == MODE_BWD_IMAGE) {
@@ -211,6 +218,11 @@ __global__ void __launch_bounds__(256, R == 4 ? 2 : 1) k_stencil(const __grid_co
         e1 = e1n;
         e2 = e2n;
     }
+    if constexpr (MODE == MODE_FWD_SUMSQ) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
+        if (((ty * T::BX + tx) & 31) == 0 && ssq != 0.f) atomicAdd(A.sumsq, (double)ssq);
+    }
 }
 
 template <int R, int MODE>
@@ -234,6 +246,7 @@ cudaError_t launch_r(int mode, const StepArgs& a, cudaStream_t s) {
         case MODE_FWD_LU: return launch_t<R, MODE_FWD_LU>(a, s);
         case MODE_BWD_GRAD: return launch_t<R, MODE_BWD_GRAD>(a, s);
         case MODE_REV: return launch_t<R, MODE_REV>(a, s);
+        case MODE_FWD_SUMSQ: return launch_t<R, MODE_FWD_SUMSQ>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }

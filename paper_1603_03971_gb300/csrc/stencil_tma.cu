@@ -332,6 +332,7 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
     const int own_off = (R + ty) * T::SW + R + V * tx;  // this vector in a u^n plane
     const int aux_off = ty * T::TX + V * tx;             // this vector in an aux plane
 
+    float ssq = 0.f;  // MODE_FWD_SUMSQ: this thread's share of the sum of squares
     // ring slots and mbarrier phases, advanced by counting
     int sc = 0, pc = 0;                          // centre plane z
     int shd = R % C::SU, phd = (R / C::SU) & 1;  // queue head plane z + R
@@ -449,7 +450,13 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
             }
             const size_t o = (size_t)z * plane + col;
             vst_stream<V>(A.u_prev + o, out);
-            if constexpr (MODE == MODE_FWD_SNAP) {
+            if constexpr (MODE == MODE_FWD_SUMSQ) {
+                if (ym && z >= A.nb && z < A.nb + A.nz) {
+#pragma unroll
+                    for (int i = 0; i < V; i++)
+                        if (x + i >= A.nb && x + i < A.nb + A.nx) ssq = fmaf(out.v[i], out.v[i], ssq);
+                }
+            } else if constexpr (MODE == MODE_FWD_SNAP) {
                 if (xm && ym && z >= A.nb && z < A.nb + A.nz)
                     vst_stream<V>(A.snap + (size_t)(z - A.nb) * slab_plane + slab_col, out);
             } else if constexpr (MODE == MODE_BWD_IMAGE) {
@@ -477,6 +484,11 @@ __global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
     }
 #pragma unroll
         for (int i = 0; i < 2 * R; i++) q[i] = q[i + G];
+    }
+    if constexpr (MODE == MODE_FWD_SUMSQ) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
+        if ((tid & 31) == 0 && ssq != 0.f) atomicAdd(A.sumsq, (double)ssq);
     }
     // a slab shorter than r issued planes [ze, zb + r) that no step waited
     // for: let those copies land before the block exits
@@ -556,6 +568,7 @@ cudaError_t launch_tma_r(int mode, const StepArgs& a, int* status, cudaStream_t 
         case MODE_FWD_LU: return launch_tma_t<R, MODE_FWD_LU>(a, status, s);
         case MODE_BWD_GRAD: return launch_tma_t<R, MODE_BWD_GRAD>(a, status, s);
         case MODE_REV: return launch_tma_t<R, MODE_REV>(a, status, s);
+        case MODE_FWD_SUMSQ: return launch_tma_t<R, MODE_FWD_SUMSQ>(a, status, s);
         default: return cudaErrorInvalidValue;
     }
 }
