@@ -1,23 +1,32 @@
 // Stencil step with TMA plane loads (tuning variant 2).
 //
 // The same leapfrog update and epilogues as k_stencil, with the plane loads
-// moved to the tensor memory accelerator: one thread issues 3D bulk tensor
-// copies of the next planes into shared-memory rings, R + P + 1 planes of
-// u^n (a 64 x 16 tile with its r-wide halo; cells outside the padded grid
-// arrive as zeros, the Dirichlet ghost cells) and P + 1 planes of the
-// pointwise operands (u^{n-1}, c, and the snapshot / accumulator of the
-// backward modes). Each ring slot has an mbarrier that the copy completes
-// (expect-tx); P planes (one or two) are in flight ahead of the one being
-// computed.
-// Each thread keeps the 2r + 1 column values of its 4-point vector in a
-// register queue, whose head it reads from the newest u^n plane in shared
-// memory. One block barrier per plane frees the slots for refilling.
+// moved to the tensor memory accelerator. A 256-thread block owns a tile of
+// x-y columns (64 x 16 at radius 4, four points per thread; 32 x 16 at
+// radius 8, two points per thread) and marches a z slab. One thread issues
+// 3D bulk tensor copies of the next planes into shared-memory rings, P
+// planes ahead of the one being computed, each slot completed on its
+// mbarrier by the copy's transaction bytes (expect-tx):
+//  - joint ring (radius-4 forward modes): R + P + 1 planes of u^n with the
+//    r-wide halo, the newest being the queue head, and P + 1 planes of the
+//    pointwise operands (u^{n-1}, c);
+//  - split ring (radius 8, radius-4 backward modes): the P + 1 centre planes
+//    of u^n with halo, while the queue head (plane z + r, no halo) travels
+//    with the pointwise operands (u^{n-1}, c, and the snapshot / accumulator
+//    of the backward modes). Cells outside the padded grid arrive as zeros:
+//    the Dirichlet ghost cells.
+// Each thread keeps the 2r + 1 column values of its points in a register
+// queue along z, moved once per G planes, and reads its x-y neighbours from
+// the centre plane in shared memory. One block barrier per plane frees the
+// slots for refilling.
 //
 // Tensor-map rules respected here: every row starts on a 16-byte boundary
 // (NX % 4 == 0), the x coordinate of every copy is a multiple of 4 floats
-// (x0 - r with x0 % 64 == 0, r % 4 == 0), boxes are at most 256 per side and
-// their rows a multiple of 16 bytes, and shared destinations are 128-byte
-// aligned. Copies only load; negative or out-of-range coordinates read zeros.
+// (x0 and x0 - r with x0 a multiple of 4: the tile width times the block
+// index, plus the launch region's x origin, which is rounded down to a
+// multiple of 4, and r % 4 == 0), boxes are at most 256 per side and their
+// rows a multiple of 16 bytes, and shared destinations are 128-byte aligned.
+// Copies only load; negative or out-of-range coordinates read zeros.
 
 #include <cuda.h>
 #include <string.h>
