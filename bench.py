@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--learned-window", type=int, default=200,
                     help="exact window: the first steps whose snapshots are recomputed from the "
                          "zero state instead of coded (checkpoint-recompute fallback)")
+    ap.add_argument("--zchunk", type=int, default=0,
+                    help="z-slab height of the main run (0: autotuned)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the library's automatic slab height instead of the autotuner")
     ap.add_argument("--no-grad", action="store_true",
                     help="skip the velocity-gradient leg (gradient_256 workload)")
     ap.add_argument("--no-boundary", action="store_true",
@@ -304,6 +308,9 @@ def learned_leg(args, dev):
     n_snap = int(data.shape[0])
     del data
     w = rtm_inputs.WORKLOADS["learned_384"]
+    # both shots run with the autotuned launch shape of this padded grid
+    tuned = (tune_shape(w.radius, w.padded_shape)
+             if args.variant == 0 and not args.no_autotune else None)
     v = w.velocity_model(device=dev).contiguous()
     rec = torch.from_numpy(w.receivers()).to(dev)
     pc = rtm.params_for(w, storage="ckpt", ckpt_every=50)
@@ -368,6 +375,7 @@ def learned_leg(args, dev):
                   "steps": args.learned_train_steps, "batch": 4, "seconds": train_s,
                   "final_loss": losses[-1][1]},
         "updates_per_shot_learned": 2 * w.nt * NX * NY * NZ,
+        "tuning": tuned,
     }
 
 
@@ -443,7 +451,7 @@ def revolve_leg(w, slots, vel, rec, dobs, dev):
     return res
 
 
-def boundary_leg(w, vel, rec, dobs, dev, ref_image, ref_shot_s, ref_ws_gb):
+def boundary_leg(w, vel, rec, dobs, dev, ref_image, ref_shot_s, ref_ws_gb, autotune=True):
     """One shot of the main workload with boundary storage: the forward pass
     keeps the model region's boundary band of every state, the backward pass
     recovers the source field by reverse time stepping (no recompute pass).
@@ -453,6 +461,8 @@ def boundary_leg(w, vel, rec, dobs, dev, ref_image, ref_shot_s, ref_ws_gb):
 
     import paper_1603_03971_gb300 as rtm
 
+    if autotune:
+        tune_shape(w.radius, w.padded_shape)  # the main run's shape (cached)
     p = rtm.params_for(w, storage="boundary")
     ws = rtm.alloc_workspace(p, dev)
     c = rtm.model_prep(p, vel, ws)
@@ -488,7 +498,15 @@ def boundary_leg(w, vel, rec, dobs, dev, ref_image, ref_shot_s, ref_ws_gb):
     return res
 
 
-def grad_leg(dev):
+def tune_shape(radius, padded_shape):
+    """Install the autotuned stencil launch shape for one padded grid."""
+    from paper_1603_03971_gb300 import autotune
+
+    choice = autotune.apply(radius, tuple(int(v) for v in padded_shape))
+    return {"zchunk": choice["zchunk"], "variant": choice["variant"]} if choice else None
+
+
+def grad_leg(dev, autotune=True):
     """The velocity gradient of the data misfit on the gradient_256 workload
     (256^3 smooth random model, 320^3 padded, 1000 steps, checkpoints every
     25): the forward pass (data + checkpoints), then rtm_grad (segment
@@ -500,6 +518,7 @@ def grad_leg(dev):
     import rtm_inputs
 
     w = rtm_inputs.WORKLOADS["gradient_256"]
+    tuned = tune_shape(w.radius, w.padded_shape) if autotune else None
     p = rtm.params_for(w, want_grad=True)
     ws = rtm.alloc_workspace(p, dev)
     c = rtm.model_prep(p, w.velocity_model(device=dev).contiguous(), ws)
@@ -534,7 +553,8 @@ def grad_leg(dev):
                        "checkpoint every %d" % (w.nt, w.ckpt_every),
            "forward_s": t_f, "gradient_s": t_g,
            "gpoint_updates_per_s": updates / (t_f + t_g) / 1e9,
-           "gradient_finite": bool(torch.isfinite(g).all()), "stencil_modes": modes}
+           "gradient_finite": bool(torch.isfinite(g).all()), "stencil_modes": modes,
+           "tuning": tuned}
     del ws
     return res
 
@@ -607,8 +627,14 @@ def run_ours(args):
     w = workload(args)
     cfg = config_of(w)
     NZ, NY, NX = w.padded_shape
-    rtm.set_tuning(w.radius, 0, args.variant)
+    rtm.set_tuning(w.radius, args.zchunk, args.variant)
     cfg["stencil_variant"] = args.variant
+    if args.zchunk > 0:
+        cfg["zchunk"] = args.zchunk
+    elif args.variant == 0 and not args.no_autotune:
+        # the library's autotuner: slab height (and plane-load path) for this
+        # padded shape, timed on a short checkpointed shot and cached
+        cfg["autotune"] = tune_shape(w.radius, w.padded_shape)
     src = shots.shot_source(rank, world, w.nx, w.ny, w.src[2]) if world > 1 else w.src
     p = rtm.params_for(w, src=src)
     rec_np = w.receivers()
@@ -705,12 +731,13 @@ def run_ours(args):
         imaging_res = imaging_leg(p, c, rec, dobs, ws, dev)
     grad_res = None
     if rank == 0 and not args.no_grad:
-        grad_res = grad_leg(dev)
+        grad_res = grad_leg(dev, autotune=args.variant == 0 and not args.no_autotune)
     boundary_res = None
     if rank == 0 and not args.no_boundary:
         ref = image / float(args.warmup + args.steps)  # one shot's checkpoint image
         boundary_res = boundary_leg(w, vel, rec, dobs, dev, ref, t_max / args.steps,
-                                    ws.numel() / 1e9)
+                                    ws.numel() / 1e9,
+                                    autotune=args.variant == 0 and not args.no_autotune)
         del ref
     revolve_res = None
     if rank == 0 and args.revolve > 0:
@@ -732,7 +759,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ws = None
         torch.cuda.empty_cache()
-        steps = 10 if NX * NY * NZ > 50_000_000 else 50
+        steps = 20 if NX * NY * NZ > 50_000_000 else 50
         s, u, threads = oracle_sample(w, vel64, steps)
         cpu = {"value": u / s / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "%d forward time steps of the FP64 oracle on the %dx%dx%d padded "

@@ -385,7 +385,8 @@ rtm_status rtm_image_filter(const rtm_params *p, const float *d_image, const flo
  *   d_data  modelled data in the same layout, or NULL.
  *   d_image [nz][ny][nx] of the full model, ACCUMULATED: each shot adds its
  *           image at its aperture, in shot order (deterministic).
- *   zchunk  z planes per work item (0: 128).
+ *   zchunk  z planes per work item (0: per wave, the tallest slab that gives
+ *           every phase step at least three items per resident block).
  * The work items march their tiles with TMA plane loads when the driver
  * provides tensor maps and rtm_set_tuning has not selected the vector-load
  * variant (1) for the radius; both kernels give the same image within the
@@ -448,7 +449,9 @@ rtm_status rtm_forward_noalloc(const rtm_params *p, const float *d_c, const int3
  * (0 = automatic) and the plane-load path (0 = automatic: TMA where the
  * driver provides tensor maps; 1 = 16-byte vector loads through registers;
  * 2 = TMA bulk tensor copies into shared-memory rings). Applies to later
- * calls on every thread. */
+ * calls on every thread, to every kernel mode on the padded grid; the
+ * reverse step of boundary storage, which covers the model region, sizes
+ * its slabs for that region. */
 rtm_status rtm_set_tuning(int32_t radius, int32_t zchunk, int32_t variant);
 
 /* Enable (1) or disable (0) per-launch CUDA-event timing of the stencil

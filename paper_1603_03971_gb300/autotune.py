@@ -1,12 +1,13 @@
 """Autotuner of the stencil launch shape.
 
-For a stencil radius and a padded grid shape it times a few forward steps of
-``rtm_forward`` (single-shot stencil) or a short ``rtm_batch`` (persistent
-multi-shot kernel) for each candidate z-slab height (and plane-load variant
-where there is more than one), with CUDA events after a warm-up, picks the
-fastest and caches the choice in a JSON file keyed by (kind, radius, shape,
-GPU name). ``apply()`` installs a cached or freshly tuned choice with
-``rtm_set_tuning``.
+For a stencil radius and a padded grid shape it times a short checkpointed
+shot of ``rtm_shot`` (forward, recompute with snapshot writes, backward with
+imaging: every kernel mode of a shot, whose best slab heights differ) or a
+short ``rtm_batch`` (persistent multi-shot kernel) for each candidate z-slab
+height (and plane-load variant where there is more than one), with CUDA
+events after a warm-up, picks the fastest and caches the choice in a JSON
+file keyed by (kind, radius, shape, GPU name). ``apply()`` installs a cached
+or freshly tuned choice with ``rtm_set_tuning``.
 """
 from __future__ import annotations
 
@@ -59,18 +60,20 @@ def candidates(NZ: int, radius: int) -> Iterable[int]:
     return sorted(out)
 
 
-def _time_forward(p, c, rec, ws, steps: int) -> float:
-    from . import forward
+def _time_shot(p, c, rec, dobs, img, ws, steps: int) -> float:
+    """Milliseconds per stencil step of a checkpointed shot (3 steps per time
+    step: forward, recompute, backward)."""
+    from . import shot
 
-    forward(p, c, rec, ws)  # warm-up
+    shot(p, c, rec, dobs, ws, img)  # warm-up
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
-    forward(p, c, rec, ws)
+    shot(p, c, rec, dobs, ws, img)
     e1.record()
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / steps
+    return e0.elapsed_time(e1) / (3 * steps)
 
 
 def tune_stencil(radius: int, padded_shape: Tuple[int, int, int], steps: int = 12,
@@ -89,18 +92,20 @@ def tune_stencil(radius: int, padded_shape: Tuple[int, int, int], steps: int = 1
     NZ, NY, NX = padded_shape
     nb = 4
     p = make_params(NX - 2 * nb, NY - 2 * nb, NZ - 2 * nb, nb, radius, steps, 10.0, 6e-4, 20.0,
-                    0.05, (1, 1, 1), 1)
+                    0.05, (1, 1, 1), 1, storage="ckpt", ckpt_every=max(1, steps // 2))
     ws = alloc_workspace(p)
     v = torch.full((p.nz, p.ny, p.nx), 3000.0, device="cuda")
     c = model_prep(p, v, ws)
     rec = torch.zeros((1, 3), dtype=torch.int32, device="cuda")
+    dobs = torch.zeros((steps, 1), device="cuda")
+    img = torch.zeros((p.nz, p.ny, p.nx), device="cuda")
     results = {}
     try:
         for variant in variants:
             for zc in candidates(NZ, radius):
                 try:
                     set_tuning(radius, zc, variant)
-                    results[(variant, zc)] = _time_forward(p, c, rec, ws, steps)
+                    results[(variant, zc)] = _time_shot(p, c, rec, dobs, img, ws, steps)
                 except RtmError:
                     continue  # a variant this driver cannot run
     finally:

@@ -312,7 +312,6 @@ struct Ctx {
     const float* ae = nullptr;  // codec parameters (learned storage)
     float* illum = nullptr;     // source illumination, model grid (+=), or NULL
     bool snap_padded = false;   // imaging snapshots are padded fields (boundary storage)
-    bool zchunk_auto = true;    // z-slab height chosen per launch region
 
     float* at(size_t off) const { return reinterpret_cast<float*>(ws + off); }
     ae::bf16* latent_slot(size_t k) const {
@@ -371,7 +370,6 @@ rtm_status make_ctx(Ctx& C, const rtm_params* p, const float* c, void* ws, rtm_s
         zc = g_zchunk[p->radius];
         var = g_variant[p->radius];
     }
-    C.zchunk_auto = zc <= 0;
     C.base.zchunk = zc > 0 ? zc : auto_zchunk(p->radius, C.d.NX, C.d.NY, C.d.NZ);
     if ((C.d.NZ + C.base.zchunk - 1) / C.base.zchunk > 65535)
         C.base.zchunk = (C.d.NZ + 65534) / 65535;  // grid.z limit
@@ -406,7 +404,10 @@ rtm_status stencil(Ctx& C, int mode, const float* cur, float* prev, float* snap,
     // the statistics count the sum-of-squares forward step as a forward step
     const int slot = mode == MODE_FWD_SUMSQ ? MODE_FWD : mode;
     set_region(a, mode);
-    if (mode == MODE_REV && C.zchunk_auto)  // slabs sized for the model region's tiles
+    // the reverse step covers the model region: its slabs are sized for its
+    // own tiles (a slab height tuned for the padded grid can leave it a
+    // nearly empty last wave)
+    if (mode == MODE_REV)
         a.zchunk = auto_zchunk(C.p->radius, a.xend - a.xorg, a.yend - a.yorg, a.zend - a.zorg);
     a.snap_padded = (mode == MODE_BWD_IMAGE && C.snap_padded) ? 1 : 0;
     bool timing;
