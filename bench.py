@@ -583,6 +583,13 @@ def batch_leg(args, dev):
                         1.0 / cfg["f0"], (0, 0, 0), 0, storage="ckpt",
                         ckpt_every=args.batch_ckpt)
     budget = 200 * 10 ** 9
+    tuned = None
+    if not args.no_autotune:  # tile rows x slab height, timed on an 8-step run
+        from paper_1603_03971_gb300 import autotune
+
+        tuned = autotune.tune_batch(p, aps, vel, nt=8, budget=budget)
+        rtm.set_tuning(p.radius, 0, tuned["variant"])
+    zchunk = tuned["zchunk"] if tuned else 0
     ws = B.alloc_workspace(p, aps, budget, device=dev)
     dobs = torch.zeros(B.data_size(p, aps), dtype=torch.float32, device=dev)
     img = torch.zeros((nz, ny, nx), dtype=torch.float32, device=dev)
@@ -590,11 +597,12 @@ def batch_leg(args, dev):
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
-    B.run(p, aps, vel, dobs, img, ws, budget=budget)
+    B.run(p, aps, vel, dobs, img, ws, budget=budget, zchunk=zchunk)
     e1.record()
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3
     rtm.check(ws)
+    rtm.set_tuning(p.radius, 0, 0)
     pts = sum((a.nx + 2 * p.nb) * (a.ny + 2 * p.nb) * (a.nz + 2 * p.nb) for a in aps)
     updates = 3 * nt * pts
     shots = ("32 shots" if args.batch_shots == "all"
@@ -603,7 +611,10 @@ def batch_leg(args, dev):
                         "layered/salt model, r=8, %d steps, checkpoint every %d"
                         % (shots, nt, args.batch_ckpt),
             "seconds": t, "gpoint_updates_per_s": updates / t / 1e9, "updates": updates,
-            "workspace_gb": ws.numel() / 1e9}
+            "workspace_gb": ws.numel() / 1e9,
+            "tuning": None if tuned is None else {
+                "tile_rows": 8 if tuned["variant"] == 3 else 16, "zchunk": tuned["zchunk"],
+                "trials_ms": tuned["trials"]}}
 
 
 # ----------------------------------------------------------------------------

@@ -446,12 +446,16 @@ rtm_status rtm_forward_noalloc(const rtm_params *p, const float *d_c, const int3
                                float *d_data, float *d_u_last, rtm_stream stream);
 
 /* Stencil tuning: z extent of the slab one thread block marches through
- * (0 = automatic) and the plane-load path (0 = automatic: TMA where the
- * driver provides tensor maps; 1 = 16-byte vector loads through registers;
- * 2 = TMA bulk tensor copies into shared-memory rings). Applies to later
+ * (0 = automatic) and the plane-load path and tile (0 = automatic: TMA
+ * where the driver provides tensor maps; 1 = 16-byte vector loads through
+ * registers; 2 = TMA bulk tensor copies into shared-memory rings, 16-row
+ * tiles of 256 threads; 3 = the same with 8-row tiles of 128 threads, five
+ * blocks per SM). Applies to later
  * calls on every thread, to every kernel mode on the padded grid; the
  * reverse step of boundary storage, which covers the model region, sizes
- * its slabs for that region. */
+ * its slabs for that region. The batched multi-shot kernel (rtm_batch)
+ * takes its plane-load path and tile from the same variant and its slab
+ * height from its own argument. */
 rtm_status rtm_set_tuning(int32_t radius, int32_t zchunk, int32_t variant);
 
 /* Enable (1) or disable (0) per-launch CUDA-event timing of the stencil

@@ -78,10 +78,11 @@ def _time_shot(p, c, rec, dobs, img, ws, steps: int) -> float:
 
 def tune_stencil(radius: int, padded_shape: Tuple[int, int, int], steps: int = 12,
                  cache_path: str = CACHE, force: bool = False,
-                 variants: Tuple[int, ...] = (1, 2)) -> dict:
-    """Best plane-load variant (1 vector loads, 2 TMA) and z-slab height for
-    the single-shot stencil on a padded grid (NZ, NY, NX), timed on a
-    constant-velocity model; trials are keyed "variant/zchunk"."""
+                 variants: Tuple[int, ...] = (1, 2, 3)) -> dict:
+    """Best plane-load path and tile (1 vector loads; 2 TMA, 16-row tiles; 3
+    TMA, 8-row tiles) and z-slab height for the single-shot stencil on a
+    padded grid (NZ, NY, NX), timed on a constant-velocity model; trials are
+    keyed "variant/zchunk"."""
     from . import RtmError, alloc_workspace, make_params, model_prep, set_tuning
 
     key = _key("stencil", radius, padded_shape)
@@ -121,10 +122,15 @@ def tune_stencil(radius: int, padded_shape: Tuple[int, int, int], steps: int = 1
 
 
 def tune_batch(p, apertures, vel: torch.Tensor, nt: int = 8, cache_path: str = CACHE,
-               force: bool = False) -> dict:
-    """Best work-item slab height of the persistent multi-shot kernel for a
-    set of apertures, timed on a short run (nt steps) of the batch."""
+               force: bool = False, variants: Tuple[int, ...] = (2, 3),
+               budget: int = 0) -> dict:
+    """Best tile (2: 16-row tiles, 3: 8-row tiles of the TMA kernel) and
+    work-item slab height (0: the per-wave automatic height) of the
+    persistent multi-shot kernel for a set of apertures, timed on a short
+    run (nt steps) of the batch under the given device-memory budget; trials
+    are keyed "variant/zchunk"."""
     from . import batch as B
+    from . import set_tuning
 
     shape = (len(apertures), max(a.nz for a in apertures), max(a.ny for a in apertures),
              max(a.nx for a in apertures))
@@ -134,23 +140,30 @@ def tune_batch(p, apertures, vel: torch.Tensor, nt: int = 8, cache_path: str = C
     if key in cache and not force:
         return cache[key]
     q = p.copy(nt=nt, ckpt_every=max(1, nt // 2))
-    ws = B.alloc_workspace(q, apertures)
+    ws = B.alloc_workspace(q, apertures, budget)
     dobs = torch.zeros(B.data_size(q, apertures), device="cuda")
     img = torch.zeros(tuple(vel.shape), device="cuda")
     NZ = max(a.nz for a in apertures) + 2 * p.nb
     results = {}
-    for zc in candidates(NZ, p.radius):
-        B.run(q, apertures, vel, dobs, img, ws, zchunk=zc)  # warm-up
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        B.run(q, apertures, vel, dobs, img, ws, zchunk=zc)
-        e1.record()
-        torch.cuda.synchronize()
-        results[zc] = e0.elapsed_time(e1)
+    try:
+        for variant in variants:
+            set_tuning(p.radius, 0, variant)
+            for zc in [0] + list(candidates(NZ, p.radius)):
+                B.run(q, apertures, vel, dobs, img, ws, budget=budget, zchunk=zc)  # warm-up
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                B.run(q, apertures, vel, dobs, img, ws, budget=budget, zchunk=zc)
+                e1.record()
+                torch.cuda.synchronize()
+                results[(variant, zc)] = e0.elapsed_time(e1)
+    finally:
+        set_tuning(p.radius, 0, 0)
+        del ws, dobs, img
+        torch.cuda.empty_cache()
     best = min(results, key=results.get)
-    choice = {"zchunk": int(best), "ms": results[best],
-              "trials": {str(k): v for k, v in results.items()}}
+    choice = {"zchunk": int(best[1]), "variant": int(best[0]), "ms": results[best],
+              "trials": {"%d/%d" % k: v for k, v in results.items()}}
     with _lock:
         cache = load_cache(cache_path)
         cache[key] = choice

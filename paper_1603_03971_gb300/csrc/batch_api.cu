@@ -115,10 +115,14 @@ rtm_status check_batch(const rtm_params* p, int nshots, const rtm_aperture* sh) 
 // the batched kernel: TMA plane loads wherever the driver provides tensor maps
 // (unless the vector-load variant is selected for the radius)
 bool batch_uses_tma(int radius) { return tma_available() && tuning_variant(radius) != 1; }
+// tile rows of the TMA kernel: 8 when the 8-row tile (variant 3) is selected
+int batch_tile_rows(int radius) { return tuning_variant(radius) == 3 ? 8 : 16; }
 
 Plan make_plan(const rtm_params* p, int nshots, const rtm_aperture* sh, size_t budget,
                int zchunk) {
-    const int tile_x = batch_uses_tma(p->radius) ? batch_tma_tile_x(p->radius) : 64;
+    const bool tma = batch_uses_tma(p->radius);
+    const int tile_x = tma ? batch_tma_tile_x(p->radius) : 64;
+    const int tile_y = tma ? batch_tile_rows(p->radius) : 16;
     Plan P;
     const int R = p->radius, k = p->ckpt_every, nt = p->nt;
     const int nseg = (nt + k - 1) / k;
@@ -134,7 +138,7 @@ Plan make_plan(const rtm_params* p, int nshots, const rtm_aperture* sh, size_t b
         b.NY = b.ny + 2 * p->nb;
         b.NZ = b.nz + 2 * p->nb;
         b.tiles_x = (b.NX + tile_x - 1) / tile_x;
-        b.tiles_y = (b.NY + 15) / 16;
+        b.tiles_y = (b.NY + tile_y - 1) / tile_y;
         b.tiles_z = (b.NZ + zchunk - 1) / zchunk;
         b.ntiles = b.tiles_x * b.tiles_y * b.tiles_z;
         b.src_x = sh[s].src_x + p->nb;
@@ -235,7 +239,8 @@ rtm_status rtm_batch(const rtm_params* p, int32_t nshots, const rtm_aperture* h_
     CUB(cudaGetDevice(&dev));
     CUB(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const bool tma = batch_uses_tma(p->radius);
-    const int bps = tma ? batch_tma_blocks_per_sm(p->radius) : batch_blocks_per_sm(p->radius);
+    const int rows = batch_tile_rows(p->radius);
+    const int bps = tma ? batch_tma_blocks_per_sm(p->radius, rows) : batch_blocks_per_sm(p->radius);
     if (bps < 1) return (rtm_status)set_error(RTM_ERR_CUDA, "batch kernel does not fit on an SM");
     int clock_khz = 0;
     CUB(cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev));
@@ -354,9 +359,9 @@ rtm_status rtm_batch(const rtm_params* p, int32_t nshots, const rtm_aperture* h_
             const int nseg = (p->nt + p->ckpt_every - 1) / p->ckpt_every;
             const int nfields = 5 + 2 * (nseg > 1 ? nseg - 1 : 0);
             for (int i = w.first; i < w.second && err == cudaSuccess; i++)
-                err = batch_tma_maps(p->radius, P.shots[i], nfields, p->ckpt_every + 1,
+                err = batch_tma_maps(p->radius, rows, P.shots[i], nfields, p->ckpt_every + 1,
                                      T->maps[i - w.first]);
-            if (err == cudaSuccess) err = launch_batch_tma(p->radius, *T, nsm * bps, s);
+            if (err == cudaSuccess) err = launch_batch_tma(p->radius, rows, *T, nsm * bps, s);
         } else {
             err = launch_batch(p->radius, A, nsm * bps, s);
         }

@@ -75,11 +75,13 @@ struct BatchTmaArgs {
     BatchArgs a;
     CUtensorMap maps[kMaxBatchShots][3];
 };
+// tile_rows: 16 (256-thread blocks) or 8 (128-thread blocks)
 int batch_tma_tile_x(int radius);
-int batch_tma_blocks_per_sm(int radius);
-cudaError_t batch_tma_maps(int radius, const BatchShot& b, int nfields, int nslabs,
-                           CUtensorMap* maps);
-cudaError_t launch_batch_tma(int radius, const BatchTmaArgs& a, int grid, cudaStream_t s);
+int batch_tma_blocks_per_sm(int radius, int tile_rows);
+cudaError_t batch_tma_maps(int radius, int tile_rows, const BatchShot& b, int nfields,
+                           int nslabs, CUtensorMap* maps);
+cudaError_t launch_batch_tma(int radius, int tile_rows, const BatchTmaArgs& a, int grid,
+                             cudaStream_t s);
 int batch_blocks_per_sm(int radius);
 cudaError_t launch_batch_prep(const BatchShot& sh, const float* vel_full, int full_nx, int full_ny,
                               int ox, int oy, int oz, double dt, float* c, float* gx, float* gy,

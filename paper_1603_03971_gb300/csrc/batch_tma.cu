@@ -2,8 +2,8 @@
 // schedule of batch.cu (phase steps of every shot in a wave, per-shot step
 // counters, bounded waits) around the plane march of the TMA stencil.
 //
-// A work item is one tile (TX x 16 columns x a z slab) of one shot at one
-// phase step. The block's thread 0 copies each plane with the 3D-in-4D bulk
+// A work item is one tile (TX columns x 16 or 8 rows x a z slab) of one shot
+// at one phase step. The block's thread 0 copies each plane with the 3D-in-4D bulk
 // tensor copy: the centre plane of u^n with its r-wide halo into a ring of
 // P + 1 slots, and, into a second ring, the tile of u^{n-1}, c, the queue head
 // (u^n at z + r, no halo) and, on imaging steps, the snapshot and image tiles.
@@ -32,10 +32,12 @@ namespace {
 
 constexpr long long kPlaneWaitLimit = 1LL << 26;
 
-template <int R>
+// tile: 16 threads along x (V points each) by BYT rows (16: 256 threads,
+// three blocks per SM; 8: 128 threads, five blocks per SM)
+template <int R, int BYT = 16>
 struct BT {
     static constexpr int V = R == 8 ? 2 : 4;  // x points per thread
-    static constexpr int BX = 16, BY = 16;
+    static constexpr int BX = 16, BY = BYT;
     static constexpr int TX = V * BX, TY = BY;
     static constexpr int SW = TX + 2 * R, SH = TY + 2 * R;
     static constexpr int HX = R / V;
@@ -45,8 +47,9 @@ struct BT {
     static constexpr int NAH = 5;  // u^{n-1}, c, queue head, snapshot, image
     static constexpr int SMEM = (NS * UPLANE + NS * NAH * APLANE) * 4;
     static constexpr int G = R == 8 ? 4 : 1;  // queue moves once per G planes
-    static constexpr int MINB = 3;
-    static_assert(R % 4 == 0 && R % V == 0 && TY >= 2 * R, "tile");
+    static constexpr int MINB = BY == 16 ? 3 : 5;
+    static_assert(R % 4 == 0 && R % V == 0 && (BY == 16 || BY == 8), "tile");
+    static_assert(MINB * (SMEM + 1024 + 1024) <= 228 * 1024, "rings do not fit the resident blocks");
 };
 
 template <int V>
@@ -180,11 +183,11 @@ struct RingPos {
 // field indices in a shot's field stack
 constexpr int F_C = 0, F_F0 = 1, F_F1 = 2, F_M0 = 3, F_M1 = 4, F_CK = 5;
 
-template <int R>
+template <int R, int BY>
 __device__ bool item_tma(const BatchTmaArgs& T, const BatchShot& S, const BatchPhase ph, int tile,
                          int s, float* uring, float* aring, uint64_t* ubar, uint64_t* abar,
                          RingPos& rp) {
-    using B = BT<R>;
+    using B = BT<R, BY>;
     constexpr int V = B::V;
     using VT = Vec<V>;
     const BatchArgs& A = T.a;
@@ -457,9 +460,10 @@ __device__ bool item_tma(const BatchTmaArgs& T, const BatchShot& S, const BatchP
     return ok;
 }
 
-template <int R>
-__global__ void __launch_bounds__(256, BT<R>::MINB) k_batch_tma(const __grid_constant__ BatchTmaArgs T) {
-    using B = BT<R>;
+template <int R, int BY>
+__global__ void __launch_bounds__(16 * BY, BT<R, BY>::MINB)
+    k_batch_tma(const __grid_constant__ BatchTmaArgs T) {
+    using B = BT<R, BY>;
     extern __shared__ __align__(128) float dsm[];
     float* uring = dsm;
     float* aring = dsm + B::NS * B::UPLANE;
@@ -498,7 +502,7 @@ __global__ void __launch_bounds__(256, BT<R>::MINB) k_batch_tma(const __grid_con
         }
         __syncthreads();
         if (!s_go) break;
-        const bool ok = item_tma<R>(T, S, A.phases[t], tile, s, uring, aring, ubar, abar, rp);
+        const bool ok = item_tma<R, BY>(T, S, A.phases[t], tile, s, uring, aring, ubar, abar, rp);
         __threadfence();
         __syncthreads();
         if (!ok) {
@@ -511,32 +515,38 @@ __global__ void __launch_bounds__(256, BT<R>::MINB) k_batch_tma(const __grid_con
 
 }  // namespace
 
+// dispatch on (radius, tile rows)
+template <class F>
+cudaError_t with_tile(int radius, int tile_rows, F&& f) {
+    if (radius == 4 && tile_rows == 16) return f(BT<4, 16>(), k_batch_tma<4, 16>);
+    if (radius == 4 && tile_rows == 8) return f(BT<4, 8>(), k_batch_tma<4, 8>);
+    if (radius == 8 && tile_rows == 16) return f(BT<8, 16>(), k_batch_tma<8, 16>);
+    if (radius == 8 && tile_rows == 8) return f(BT<8, 8>(), k_batch_tma<8, 8>);
+    return cudaErrorInvalidValue;
+}
+
 int batch_tma_tile_x(int radius) { return radius == 8 ? BT<8>::TX : BT<4>::TX; }
 
-int batch_tma_blocks_per_sm(int radius) {
+int batch_tma_blocks_per_sm(int radius, int tile_rows) {
     int n = 0;
-    if (radius == 4) {
-        if (cudaFuncSetAttribute(k_batch_tma<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 BT<4>::SMEM) != cudaSuccess)
-            return 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_tma<4>, 256, BT<4>::SMEM);
-    } else {
-        if (cudaFuncSetAttribute(k_batch_tma<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 BT<8>::SMEM) != cudaSuccess)
-            return 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_tma<8>, 256, BT<8>::SMEM);
-    }
-    return n;
+    const cudaError_t e = with_tile(radius, tile_rows, [&](auto b, auto kernel) {
+        using B = decltype(b);
+        cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             B::SMEM);
+        if (r != cudaSuccess) return r;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, 16 * B::BY, B::SMEM);
+    });
+    return e == cudaSuccess ? n : 0;
 }
 
 // the three tensor maps of one shot: halo tile and plain tile over its field
 // stack, plain tile over its slab stack
-cudaError_t batch_tma_maps(int radius, const BatchShot& b, int nfields, int nslabs,
-                           CUtensorMap* maps) {
+cudaError_t batch_tma_maps(int radius, int tile_rows, const BatchShot& b, int nfields,
+                           int nslabs, CUtensorMap* maps) {
     EncodeTiledFn f = tma_encoder();
     if (!f) return cudaErrorNotSupported;
     const int TX = radius == 8 ? BT<8>::TX : BT<4>::TX;
-    const int TY = 16;
+    const int TY = tile_rows;
     const cuuint64_t fd[4] = {(cuuint64_t)b.NX, (cuuint64_t)b.NY, (cuuint64_t)b.NZ,
                               (cuuint64_t)nfields};
     const cuuint64_t fs[3] = {(cuuint64_t)b.NX * 4, (cuuint64_t)b.NX * b.NY * 4,
@@ -563,20 +573,22 @@ cudaError_t batch_tma_maps(int radius, const BatchShot& b, int nfields, int nsla
     return cudaSuccess;
 }
 
-cudaError_t launch_batch_tma(int radius, const BatchTmaArgs& a, int grid, cudaStream_t s) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(16, 16);
-    cfg.dynamicSmemBytes = radius == 8 ? BT<8>::SMEM : BT<4>::SMEM;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (radius == 4) return cudaLaunchKernelEx(&cfg, k_batch_tma<4>, a);
-    if (radius == 8) return cudaLaunchKernelEx(&cfg, k_batch_tma<8>, a);
-    return cudaErrorInvalidValue;
+cudaError_t launch_batch_tma(int radius, int tile_rows, const BatchTmaArgs& a, int grid,
+                             cudaStream_t s) {
+    return with_tile(radius, tile_rows, [&](auto b, auto kernel) {
+        using B = decltype(b);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(16, B::BY);
+        cfg.dynamicSmemBytes = B::SMEM;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, kernel, a);
+    });
 }
 
 }  // namespace rtm

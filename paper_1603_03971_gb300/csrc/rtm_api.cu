@@ -420,13 +420,15 @@ rtm_status stencil(Ctx& C, int mode, const float* cur, float* prev, float* snap,
     if (timing) {
         PendingTiming t{t_timer.get(), t_timer.get(), slot, stencil_bytes(C, slot)};
         CU(cudaEventRecord(t.a, C.s));
-        CU(C.variant == 2 ? launch_stencil_tma(C.p->radius, mode, a, C.status(), C.s)
+        CU(C.variant >= 2 ? launch_stencil_tma(C.p->radius, mode, a, C.status(), C.s,
+                                               C.variant == 3 ? 8 : 16)
                           : launch_stencil(C.p->radius, mode, a, C.s));
         CU(cudaEventRecord(t.b, C.s));
         t_timer.pending.push_back(t);
         if (t_timer.pending.size() >= 2048) CHECK(t_timer.drain(C.s));
     } else {
-        CU(C.variant == 2 ? launch_stencil_tma(C.p->radius, mode, a, C.status(), C.s)
+        CU(C.variant >= 2 ? launch_stencil_tma(C.p->radius, mode, a, C.status(), C.s,
+                                               C.variant == 3 ? 8 : 16)
                           : launch_stencil(C.p->radius, mode, a, C.s));
     }
     return RTM_OK;
@@ -1137,7 +1139,7 @@ rtm_status rtm_check(void* d_ws, size_t ws_bytes, rtm_stream stream) {
 
 rtm_status rtm_set_tuning(int32_t radius, int32_t zchunk, int32_t variant) {
     if (radius != 4 && radius != 8) return fail(RTM_ERR_UNSUPPORTED, "radius %d", radius);
-    if (zchunk < 0 || variant < 0 || variant > 2)
+    if (zchunk < 0 || variant < 0 || variant > 3)
         return fail(RTM_ERR_INVALID, "zchunk %d / variant %d out of range", zchunk, variant);
     std::lock_guard<std::mutex> lk(g_mu);
     g_zchunk[radius] = zchunk;

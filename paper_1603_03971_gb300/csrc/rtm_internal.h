@@ -70,8 +70,9 @@ inline void set_region(StepArgs& a, int mode) {
 
 cudaError_t launch_stencil(int radius, int mode, const StepArgs& a, cudaStream_t s);
 // the same step with TMA plane loads (tuning variant 2); status: device status word
+// tile_rows: 16 (256-thread blocks) or 8 (128-thread blocks)
 cudaError_t launch_stencil_tma(int radius, int mode, const StepArgs& a, int* status,
-                               cudaStream_t s);
+                               cudaStream_t s, int tile_rows = 16);
 bool tma_available();
 int auto_zchunk(int radius, int NX, int NY, int NZ);
 

@@ -55,17 +55,20 @@ __host__ __device__ constexpr int points_per_thread() {
     return R == 8 ? 2 : 4;
 }
 
-template <int R, int V>
+// tile: 16 threads along x (V floats each) by BYT rows, one row per thread
+// (16 rows: 256 threads, the default; 8 rows: 128 threads, more blocks per SM
+// and twice the y halo per row, an autotuner choice)
+template <int R, int V, int BYT = 16>
 struct TmaTile {
     static constexpr int BX = 16;          // threads along x, V floats each
-    static constexpr int BY = 16;          // threads along y
+    static constexpr int BY = BYT;         // threads along y
     static constexpr int TX = V * BX;      // floats
     static constexpr int TY = BY;          // rows
     static constexpr int SW = TX + 2 * R;  // shared row width (floats)
     static constexpr int SH = TY + 2 * R;  // shared rows
     static constexpr int HX = R / V;       // halo vectors per side per row
     static_assert(R % 4 == 0 && R % V == 0, "radius must be a multiple of 4 and of V");
-    static_assert(TY >= 2 * R, "tile too short");
+    static_assert(BY == 16 || BY == 8, "16- or 8-row tiles");
 };
 
 template <int V>
@@ -186,9 +189,9 @@ __host__ __device__ constexpr int queue_group() {
     return R == 8 ? kQueueGroup8 : kQueueGroup4;
 }
 
-template <int R, int MODE>
+template <int R, int MODE, int BY = 16>
 struct TmaCfg {
-    using T = TmaTile<R, points_per_thread<R>()>;
+    using T = TmaTile<R, points_per_thread<R>(), BY>;
     static constexpr bool SPLIT = split_ring<R, MODE>();
     static constexpr int NA = aux_planes<MODE>();
     static constexpr int NAH = NA + (SPLIT ? 1 : 0);  // aux ring entries per plane
@@ -237,26 +240,27 @@ __device__ __forceinline__ void tma3(float* dst, const CUtensorMap* map, int x, 
 }
 
 // resident blocks per SM, with the registers capped at 80 per thread for
-// three: at radius 4 the forward modes need 73 KB of shared memory (three
-// fit), the backward modes 98 KB (two); at radius 8 the split ring needs
-// 36-48 KB (three)
-template <int R, int MODE>
+// three 256-thread blocks: at radius 4 the forward modes need 73 KB of
+// shared memory (three fit), the split-ring backward modes 54 KB; at radius 8
+// the split ring needs 36-48 KB. 8-row tiles (128 threads, 23-45 KB): five
+template <int R, int MODE, int BY = 16>
 constexpr int tma_min_blocks() {
-    return 3;
+    return BY == 16 ? 3 : 5;
 }
 // the rings of the resident blocks fit the SM's 228 KB (1 KB reserved per block)
-template <int R, int MODE>
+template <int R, int MODE, int BY = 16>
 constexpr bool rings_fit() {
-    return tma_min_blocks<R, MODE>() * (TmaCfg<R, MODE>::SMEM + 1024 + 256) <= 228 * 1024;
+    return tma_min_blocks<R, MODE, BY>() * (TmaCfg<R, MODE, BY>::SMEM + 1024 + 256) <=
+           228 * 1024;
 }
 
-template <int R, int MODE>
-__global__ void __launch_bounds__(256, (tma_min_blocks<R, MODE>()))
+template <int R, int MODE, int BY>
+__global__ void __launch_bounds__(16 * BY, (tma_min_blocks<R, MODE, BY>()))
     k_stencil_tma(const __grid_constant__ StepArgs A, const __grid_constant__ TmaMaps M, int* status) {
     constexpr int V = points_per_thread<R>();
-    using T = TmaTile<R, V>;
+    using T = TmaTile<R, V, BY>;
     using VT = Vec<V>;
-    using C = TmaCfg<R, MODE>;
+    using C = TmaCfg<R, MODE, BY>;
     constexpr int NA = C::NA;
     extern __shared__ __align__(128) float dsm[];
     float* uring = dsm;
@@ -523,17 +527,17 @@ cudaError_t make_map(CUtensorMap* m, const float* base, int nx, int ny, int nz, 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int R, int MODE>
+template <int R, int MODE, int BY>
 cudaError_t launch_tma_t(const StepArgs& a, int* status, cudaStream_t s) {
-    using T = TmaTile<R, points_per_thread<R>()>;
-    constexpr int smem = TmaCfg<R, MODE>::SMEM;
-    static_assert(rings_fit<R, MODE>(), "rings do not fit the resident blocks");
+    using T = TmaTile<R, points_per_thread<R>(), BY>;
+    constexpr int smem = TmaCfg<R, MODE, BY>::SMEM;
+    static_assert(rings_fit<R, MODE, BY>(), "rings do not fit the resident blocks");
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_stencil_tma<R, MODE>,
+        cudaError_t e = cudaFuncSetAttribute(k_stencil_tma<R, MODE, BY>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_stencil_tma<R, MODE>,
+        e = cudaFuncSetAttribute(k_stencil_tma<R, MODE, BY>,
                                  cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
@@ -545,7 +549,7 @@ cudaError_t launch_tma_t(const StepArgs& a, int* status, cudaStream_t s) {
     if ((e = make_map(&M.u, a.u_cur, a.NX, a.NY, a.NZ, T::TX + 2 * R, T::TY + 2 * R)) != cudaSuccess)
         return e;
     if ((e = make_map(&M.prev, a.u_prev, a.NX, a.NY, a.NZ, T::TX, T::TY)) != cudaSuccess) return e;
-    if (TmaCfg<R, MODE>::SPLIT &&
+    if (TmaCfg<R, MODE, BY>::SPLIT &&
         (e = make_map(&M.uh, a.u_cur, a.NX, a.NY, a.NZ, T::TX, T::TY)) != cudaSuccess)
         return e;
     if ((e = make_map(&M.c, a.c, a.NX, a.NY, a.NZ, T::TX, T::TY)) != cudaSuccess) return e;
@@ -564,20 +568,20 @@ cudaError_t launch_tma_t(const StepArgs& a, int* status, cudaStream_t s) {
               (a.zend - a.zorg + a.zchunk - 1) / a.zchunk);
     if (a.xorg % 4 || a.xend <= a.xorg || a.yend <= a.yorg || a.zend <= a.zorg)
         return cudaErrorInvalidValue;
-    k_stencil_tma<R, MODE><<<grid, block, smem, s>>>(a, M, status);
+    k_stencil_tma<R, MODE, BY><<<grid, block, smem, s>>>(a, M, status);
     return cudaGetLastError();
 }
 
-template <int R>
+template <int R, int BY>
 cudaError_t launch_tma_r(int mode, const StepArgs& a, int* status, cudaStream_t s) {
     switch (mode) {
-        case MODE_FWD: return launch_tma_t<R, MODE_FWD>(a, status, s);
-        case MODE_FWD_SNAP: return launch_tma_t<R, MODE_FWD_SNAP>(a, status, s);
-        case MODE_BWD_IMAGE: return launch_tma_t<R, MODE_BWD_IMAGE>(a, status, s);
-        case MODE_FWD_LU: return launch_tma_t<R, MODE_FWD_LU>(a, status, s);
-        case MODE_BWD_GRAD: return launch_tma_t<R, MODE_BWD_GRAD>(a, status, s);
-        case MODE_REV: return launch_tma_t<R, MODE_REV>(a, status, s);
-        case MODE_FWD_SUMSQ: return launch_tma_t<R, MODE_FWD_SUMSQ>(a, status, s);
+        case MODE_FWD: return launch_tma_t<R, MODE_FWD, BY>(a, status, s);
+        case MODE_FWD_SNAP: return launch_tma_t<R, MODE_FWD_SNAP, BY>(a, status, s);
+        case MODE_BWD_IMAGE: return launch_tma_t<R, MODE_BWD_IMAGE, BY>(a, status, s);
+        case MODE_FWD_LU: return launch_tma_t<R, MODE_FWD_LU, BY>(a, status, s);
+        case MODE_BWD_GRAD: return launch_tma_t<R, MODE_BWD_GRAD, BY>(a, status, s);
+        case MODE_REV: return launch_tma_t<R, MODE_REV, BY>(a, status, s);
+        case MODE_FWD_SUMSQ: return launch_tma_t<R, MODE_FWD_SUMSQ, BY>(a, status, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -601,11 +605,18 @@ EncodeTiledFn tma_encoder() {
 bool tma_available() { return tma_encoder() != nullptr; }
 
 cudaError_t launch_stencil_tma(int radius, int mode, const StepArgs& a, int* status,
-                               cudaStream_t s) {
-    if (a.zchunk < 1) return cudaErrorInvalidValue;
+                               cudaStream_t s, int tile_rows) {
+    if (a.zchunk < 1 || (tile_rows != 16 && tile_rows != 8)) return cudaErrorInvalidValue;
+    if (tile_rows == 8) {
+        switch (radius) {
+            case 4: return launch_tma_r<4, 8>(mode, a, status, s);
+            case 8: return launch_tma_r<8, 8>(mode, a, status, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (radius) {
-        case 4: return launch_tma_r<4>(mode, a, status, s);
-        case 8: return launch_tma_r<8>(mode, a, status, s);
+        case 4: return launch_tma_r<4, 16>(mode, a, status, s);
+        case 8: return launch_tma_r<8, 16>(mode, a, status, s);
         default: return cudaErrorInvalidValue;
     }
 }

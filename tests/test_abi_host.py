@@ -103,6 +103,7 @@ def test_calls_reject_bad_arguments_without_a_device():
     assert L.rtm_misfit(fake, fake, -1, None, fake, None) == 1
     assert L.rtm_set_tuning(6, 0, 0) == 7
     assert L.rtm_set_tuning(4, -1, 0) == 1
+    assert L.rtm_set_tuning(4, 0, 4) == 1  # variants 0..3
     assert L.rtm_ae_set_decoder(3) == 1
     assert L.rtm_ae_set_decoder(-1) == 1
     assert L.rtm_ae_set_decoder(0) == 0

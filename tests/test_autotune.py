@@ -32,9 +32,31 @@ def test_tune_stencil_picks_the_fastest_and_caches(tmp_path):
     path = str(tmp_path / "tune.json")
     choice = autotune.tune_stencil(4, (104, 104, 104), steps=6, cache_path=path)
     trials = {tuple(int(x) for x in k.split("/")): v for k, v in choice["trials"].items()}
-    assert {v for v, _ in trials} == {1, 2}  # both plane-load variants timed
+    assert {v for v, _ in trials} == {1, 2, 3}  # vector loads, TMA 16-row and 8-row tiles
     assert (choice["variant"], choice["zchunk"]) == min(trials, key=trials.get)
     cached = json.load(open(path))
     assert any(v["zchunk"] == choice["zchunk"] for v in cached.values())
     # the second call is served from the cache
     assert autotune.tune_stencil(4, (104, 104, 104), cache_path=path) == choice
+
+
+@pytest.mark.gpu
+def test_tune_batch_sweeps_tiles_and_slabs(tmp_path):
+    import torch
+
+    import paper_1603_03971_gb300 as rtm
+    from paper_1603_03971_gb300 import batch as B
+
+    path = str(tmp_path / "tune.json")
+    nz, ny, nx = 48, 40, 56
+    p = rtm.make_params(nx, ny, nz, 4, 8, 8, 10.0, 6e-4, 25.0, 0.04, (0, 0, 0), 0,
+                        storage="ckpt", ckpt_every=4)
+    aps = [B.Aperture(0, 0, 0, 40, 32, 32, 20, 16, 3, 2),
+           B.Aperture(8, 4, 8, 48, 36, 40, 24, 18, 4, 2)]
+    vel = torch.full((nz, ny, nx), 2500.0, device="cuda")
+    choice = autotune.tune_batch(p, aps, vel, nt=4, cache_path=path)
+    trials = {tuple(int(x) for x in k.split("/")): v for k, v in choice["trials"].items()}
+    assert {v for v, _ in trials} == {2, 3}
+    assert (0 in {z for _, z in trials})  # the per-wave automatic height
+    assert (choice["variant"], choice["zchunk"]) == min(trials, key=trials.get)
+    assert autotune.tune_batch(p, aps, vel, cache_path=path) == choice

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-4
 
 
-@pytest.fixture(autouse=True, params=[0, 1], ids=["tma", "vector"])
+@pytest.fixture(autouse=True, params=[0, 3, 1], ids=["tma", "tma8", "vector"])
 def kernel_variant(request):
     import paper_1603_03971_gb300 as rtm
 

@@ -34,7 +34,7 @@ def _image(case, d_obs=None):
     return g, d_obs, img.cpu().numpy().astype(np.float64), adj.cpu().numpy()
 
 
-@pytest.mark.parametrize("variant", [2, 1])
+@pytest.mark.parametrize("variant", [2, 3, 1])
 @pytest.mark.parametrize("r,ie,nt,shape", [
     (4, 1, 60, SMALL), (4, 3, 61, RAGGED), (8, 1, 50, dict(nx=36, ny=34, nz=35, nb=8)),
     (8, 2, 44, RAGGED), (4, 1, 40, THIN)])

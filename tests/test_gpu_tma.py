@@ -24,20 +24,22 @@ def _tma():
     rtm.set_tuning(8, 0, 0)
 
 
-def _use(r, zchunk):
+def _use(r, zchunk, variant=2):
     import paper_1603_03971_gb300 as rtm
 
-    rtm.set_tuning(r, zchunk, 2)
+    rtm.set_tuning(r, zchunk, variant)
 
 
+# variant 2: 16-row tiles (256 threads); variant 3: 8-row tiles (128 threads)
+@pytest.mark.parametrize("variant", [2, 3])
 @pytest.mark.parametrize("r", [4, 8])
 @pytest.mark.parametrize("shape", list(SHAPES))
 @pytest.mark.parametrize("zchunk", [0, 16, 5])
-def test_tma_forward_parity(r, shape, zchunk):
+def test_tma_forward_parity(r, shape, zchunk, variant):
     case = Case(r=r, nt=40, **SHAPES[shape])
     if shape == "thin":
         case.rec_stride = 1
-    _use(r, zchunk)
+    _use(r, zchunk, variant)
     g = GpuRun(case)
     data, last = g.forward(keep_last=True)
     ref = case.oracle_problem().forward(keep_last=True)
@@ -45,10 +47,11 @@ def test_tma_forward_parity(r, shape, zchunk):
     assert rel_l2(last[1].cpu().numpy(), ref["last"][1]) <= TOL
 
 
+@pytest.mark.parametrize("variant", [2, 3])
 @pytest.mark.parametrize("r,storage,ck", [(4, "ckpt", 16), (8, "all", 0)])
-def test_tma_backward_image_parity(r, storage, ck):
+def test_tma_backward_image_parity(r, storage, ck, variant):
     case = Case(r=r, nt=50, storage=storage, ckpt_every=ck, **SHAPES["ragged"])
-    _use(r, 0)
+    _use(r, 0, variant)
     g = GpuRun(case)
     g.forward()
     d_obs = case.d_obs(g.nrec)
@@ -60,9 +63,10 @@ def test_tma_backward_image_parity(r, storage, ck):
     assert rel_l2(adj.cpu().numpy(), bw["src_adj"]) <= TOL
 
 
-def test_tma_gradient_parity():
+@pytest.mark.parametrize("variant", [2, 3])
+def test_tma_gradient_parity(variant):
     case = Case(r=4, nt=40, storage="ckpt", ckpt_every=9, **SHAPES["small"])
-    _use(4, 0)
+    _use(4, 0, variant)
     g = GpuRun(case, want_grad=True, squared=True)
     g.forward()
     resid = case.d_obs(g.nrec)
@@ -78,9 +82,11 @@ def test_tma_agrees_with_vector_loads():
 
     case = Case(r=4, nt=30, **SHAPES["ragged"])
     out = []
-    for variant in (1, 2):
+    for variant in (1, 2, 3):
         rtm.set_tuning(4, 0, variant)
         g = GpuRun(case)
         data, last = g.forward(keep_last=True)
         out.append(last.cpu().numpy())
     assert rel_l2(out[1], out[0]) <= 1e-6
+    # the tile shape changes no arithmetic
+    assert np.array_equal(out[2], out[1])
