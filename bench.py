@@ -84,7 +84,8 @@ def parse():
                     help="also time one shot of the main workload with binomial checkpointing "
                          "in SLOTS checkpoint slots")
     ap.add_argument("--variant", type=int, default=0,
-                    help="stencil plane-load variant: 0 automatic, 1 vector loads, 2 TMA")
+                    help="stencil plane-load variant and tile: 0 automatic, 1 vector loads, "
+                         "2 TMA 16-row tiles, 3 TMA 8-row tiles")
     return ap.parse_args()
 
 
@@ -204,15 +205,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def profiled_traffic():
+def profiled_traffic(tile_rows: int):
     """DRAM bytes per launch of the backward imaging stencil from the committed
-    ncu summary, if it was taken on the current kernel source."""
+    ncu summary, if it was taken on the current kernel source with the same
+    tile."""
     if not os.path.exists(PROFILE):
         return None
     text = open(PROFILE).read()
     m_t = re.search(r"traffic_bytes_per_launch:\s*([\d.eE+]+)", text)
     m_h = re.search(r"stencil_source_sha256:\s*([0-9a-f]{64})", text)
-    if not (m_t and m_h):
+    m_r = re.search(r"tile_rows:\s*(\d+)", text)
+    if not (m_t and m_h and m_r) or int(m_r.group(1)) != tile_rows:
         return None
     cur = hashlib.sha256(open(STENCIL_SRC, "rb").read()).hexdigest()
     if cur != m_h.group(1):
@@ -702,13 +705,16 @@ def run_ours(args):
     per_launch_s = b["ms"] / max(launches, 1) / 1e3
     achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else None
     shares = {k: v["ms"] for k, v in st["stencil"].items() if v["launches"]}
+    variant = args.variant or (cfg.get("autotune") or {}).get("variant", 0)
+    tile_rows = 8 if variant == 3 else 16
     roofline = {
-        "kernel": ("k_stencil_tma<%d, MODE_BWD_IMAGE>" if args.variant != 1 else
-                   "k_stencil<%d, MODE_BWD_IMAGE>") % w.radius
+        "kernel": ("k_stencil_tma<%d, MODE_BWD_IMAGE, %d-row tiles>" % (w.radius, tile_rows)
+                   if variant != 1 else "k_stencil<%d, MODE_BWD_IMAGE>" % w.radius)
                   + " (backward step + fused zero-lag imaging)",
         "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
         "frac": (achieved / hbm) if achieved else None, "peak_kind": peak_kind,
-        "traffic": profiled_traffic(), "algorithmic_bytes_per_launch": per_launch_bytes,
+        "traffic": profiled_traffic(tile_rows) if variant != 1 else None,
+        "algorithmic_bytes_per_launch": per_launch_bytes,
         "launch_ms": per_launch_s * 1e3,
         "stencil_ms_per_step": {k: v / args.steps for k, v in shares.items()},
     }
