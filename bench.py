@@ -205,17 +205,21 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def profiled_traffic(tile_rows: int):
+def profiled_traffic(radius: int, tile_rows: int, padded_shape):
     """DRAM bytes per launch of the backward imaging stencil from the committed
     ncu summary, if it was taken on the current kernel source with the same
-    tile."""
+    radius and tile and scaled to this padded grid."""
     if not os.path.exists(PROFILE):
         return None
     text = open(PROFILE).read()
     m_t = re.search(r"traffic_bytes_per_launch:\s*([\d.eE+]+)", text)
     m_h = re.search(r"stencil_source_sha256:\s*([0-9a-f]{64})", text)
     m_r = re.search(r"tile_rows:\s*(\d+)", text)
-    if not (m_t and m_h and m_r) or int(m_r.group(1)) != tile_rows:
+    m_s = re.search(r"radius:\s*(\d+)", text)
+    m_g = re.search(r"padded_grid:\s*([\dx]+)", text)
+    if not (m_t and m_h and m_r and m_s and m_g) or int(m_r.group(1)) != tile_rows \
+            or int(m_s.group(1)) != radius \
+            or m_g.group(1) != "x".join(str(int(n)) for n in padded_shape):
         return None
     cur = hashlib.sha256(open(STENCIL_SRC, "rb").read()).hexdigest()
     if cur != m_h.group(1):
@@ -713,7 +717,8 @@ def run_ours(args):
                   + " (backward step + fused zero-lag imaging)",
         "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
         "frac": (achieved / hbm) if achieved else None, "peak_kind": peak_kind,
-        "traffic": profiled_traffic(tile_rows) if variant != 1 else None,
+        "traffic": (profiled_traffic(w.radius, tile_rows, w.padded_shape)
+                    if variant != 1 else None),
         "algorithmic_bytes_per_launch": per_launch_bytes,
         "launch_ms": per_launch_s * 1e3,
         "stencil_ms_per_step": {k: v / args.steps for k, v in shares.items()},
