@@ -449,8 +449,9 @@ rtm_status rtm_forward_noalloc(const rtm_params *p, const float *d_c, const int3
  * (0 = automatic) and the plane-load path and tile (0 = automatic: TMA
  * where the driver provides tensor maps; 1 = 16-byte vector loads through
  * registers; 2 = TMA bulk tensor copies into shared-memory rings, 16-row
- * tiles of 256 threads; 3 = the same with 8-row tiles of 128 threads, five
- * blocks per SM). Applies to later
+ * tiles of 256 threads; 3 = the same with 8-row tiles of 128 threads and
+ * 4-point vectors at both radii, five blocks per SM at radius 4, four at
+ * radius 8). Applies to later
  * calls on every thread, to every kernel mode on the padded grid; the
  * reverse step of boundary storage, which covers the model region, sizes
  * its slabs for that region. The batched multi-shot kernel (rtm_batch)

@@ -121,8 +121,8 @@ int batch_tile_rows(int radius) { return tuning_variant(radius) == 3 ? 8 : 16; }
 Plan make_plan(const rtm_params* p, int nshots, const rtm_aperture* sh, size_t budget,
                int zchunk) {
     const bool tma = batch_uses_tma(p->radius);
-    const int tile_x = tma ? batch_tma_tile_x(p->radius) : 64;
     const int tile_y = tma ? batch_tile_rows(p->radius) : 16;
+    const int tile_x = tma ? batch_tma_tile_x(p->radius, tile_y) : 64;
     Plan P;
     const int R = p->radius, k = p->ckpt_every, nt = p->nt;
     const int nseg = (nt + k - 1) / k;

@@ -76,7 +76,7 @@ struct BatchTmaArgs {
     CUtensorMap maps[kMaxBatchShots][3];
 };
 // tile_rows: 16 (256-thread blocks) or 8 (128-thread blocks)
-int batch_tma_tile_x(int radius);
+int batch_tma_tile_x(int radius, int tile_rows);
 int batch_tma_blocks_per_sm(int radius, int tile_rows);
 cudaError_t batch_tma_maps(int radius, int tile_rows, const BatchShot& b, int nfields,
                            int nslabs, CUtensorMap* maps);

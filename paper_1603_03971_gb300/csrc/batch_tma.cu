@@ -33,10 +33,11 @@ namespace {
 constexpr long long kPlaneWaitLimit = 1LL << 26;
 
 // tile: 16 threads along x (V points each) by BYT rows (16: 256 threads,
-// three blocks per SM; 8: 128 threads, five blocks per SM)
+// three blocks per SM; 8: 128 threads, five blocks per SM at radius 4 and
+// four at radius 8, where the 8-row tiles keep 4-point vectors)
 template <int R, int BYT = 16>
 struct BT {
-    static constexpr int V = R == 8 ? 2 : 4;  // x points per thread
+    static constexpr int V = (R == 8 && BYT == 16) ? 2 : 4;  // x points per thread
     static constexpr int BX = 16, BY = BYT;
     static constexpr int TX = V * BX, TY = BY;
     static constexpr int SW = TX + 2 * R, SH = TY + 2 * R;
@@ -46,8 +47,8 @@ struct BT {
     static constexpr int UPLANE = SH * SW, APLANE = TY * TX;
     static constexpr int NAH = 5;  // u^{n-1}, c, queue head, snapshot, image
     static constexpr int SMEM = (NS * UPLANE + NS * NAH * APLANE) * 4;
-    static constexpr int G = R == 8 ? 4 : 1;  // queue moves once per G planes
-    static constexpr int MINB = BY == 16 ? 3 : 5;
+    static constexpr int G = R == 8 ? (V == 2 ? 4 : 2) : 1;  // queue moves once per G planes
+    static constexpr int MINB = BY == 16 ? 3 : (R == 8 ? 4 : 5);
     static_assert(R % 4 == 0 && R % V == 0 && (BY == 16 || BY == 8), "tile");
     static_assert(MINB * (SMEM + 1024 + 1024) <= 228 * 1024, "rings do not fit the resident blocks");
 };
@@ -525,7 +526,14 @@ cudaError_t with_tile(int radius, int tile_rows, F&& f) {
     return cudaErrorInvalidValue;
 }
 
-int batch_tma_tile_x(int radius) { return radius == 8 ? BT<8>::TX : BT<4>::TX; }
+int batch_tma_tile_x(int radius, int tile_rows) {
+    int tx = 0;
+    with_tile(radius, tile_rows, [&](auto b, auto) {
+        tx = decltype(b)::TX;
+        return cudaSuccess;
+    });
+    return tx;
+}
 
 int batch_tma_blocks_per_sm(int radius, int tile_rows) {
     int n = 0;
@@ -545,8 +553,9 @@ cudaError_t batch_tma_maps(int radius, int tile_rows, const BatchShot& b, int nf
                            int nslabs, CUtensorMap* maps) {
     EncodeTiledFn f = tma_encoder();
     if (!f) return cudaErrorNotSupported;
-    const int TX = radius == 8 ? BT<8>::TX : BT<4>::TX;
+    const int TX = batch_tma_tile_x(radius, tile_rows);
     const int TY = tile_rows;
+    if (TX == 0) return cudaErrorInvalidValue;
     const cuuint64_t fd[4] = {(cuuint64_t)b.NX, (cuuint64_t)b.NY, (cuuint64_t)b.NZ,
                               (cuuint64_t)nfields};
     const cuuint64_t fs[3] = {(cuuint64_t)b.NX * 4, (cuuint64_t)b.NX * b.NY * 4,

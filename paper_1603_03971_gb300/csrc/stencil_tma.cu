@@ -47,12 +47,15 @@ struct TmaMaps {
     CUtensorMap u, prev, c, e1, e2, uh;  // uh: u^n without halo (queue heads)
 };
 
-// V consecutive x points per thread: 4 (16-byte vectors) at radius 4; 2 at
-// radius 8, where the 2r + 1 deep register queue of 4-point vectors would
-// hold a block to one per SM
-template <int R>
+// V consecutive x points per thread: 4 (16-byte vectors), except in the
+// 16-row tiles at radius 8, whose 256-thread blocks hold 2 (the 2r + G deep
+// register queue of 4-point vectors would allow one block per SM). The 8-row
+// radius-8 tiles keep 4 points per thread: 128 registers, four blocks of 128
+// threads per SM, and half the per-plane overhead and shared-memory x loads
+// per point
+template <int R, int BY = 16>
 __host__ __device__ constexpr int points_per_thread() {
-    return R == 8 ? 2 : 4;
+    return (R == 8 && BY == 16) ? 2 : 4;
 }
 
 // tile: 16 threads along x (V floats each) by BYT rows, one row per thread
@@ -179,19 +182,18 @@ __host__ __device__ constexpr int tma_prefetch() {
 
 // the register queue moves once per G planes (2r + G entries, the plane body
 // unrolled G times): 2r / G vector moves per plane instead of 2r. 576^3,
-// radius 8: G = 1 / 2 / 4 gave 204.8 / 210.6 / 215.8 Gpoint-updates/s;
-// radius 4: G = 1 / 2 gave 318.4 / 320.8 (G = 3 spills under the 80-register
-// cap of three blocks per SM)
-constexpr int kQueueGroup8 = 4;
-constexpr int kQueueGroup4 = 2;
-template <int R>
+// radius 8, 2-point vectors: G = 1 / 2 / 4 gave 204.8 / 210.6 / 215.8
+// Gpoint-updates/s; radius 4: G = 1 / 2 gave 318.4 / 320.8 (G = 3 spills
+// under the 80-register cap of three blocks per SM). Radius 8 with 4-point
+// vectors keeps G = 2 (the queue is 72 registers)
+template <int R, int V>
 __host__ __device__ constexpr int queue_group() {
-    return R == 8 ? kQueueGroup8 : kQueueGroup4;
+    return (R == 8 && V == 2) ? 4 : 2;
 }
 
 template <int R, int MODE, int BY = 16>
 struct TmaCfg {
-    using T = TmaTile<R, points_per_thread<R>(), BY>;
+    using T = TmaTile<R, points_per_thread<R, BY>(), BY>;
     static constexpr bool SPLIT = split_ring<R, MODE>();
     static constexpr int NA = aux_planes<MODE>();
     static constexpr int NAH = NA + (SPLIT ? 1 : 0);  // aux ring entries per plane
@@ -239,13 +241,15 @@ __device__ __forceinline__ void tma3(float* dst, const CUtensorMap* map, int x, 
         : "memory");
 }
 
-// resident blocks per SM, with the registers capped at 80 per thread for
-// three 256-thread blocks: at radius 4 the forward modes need 73 KB of
-// shared memory (three fit), the split-ring backward modes 54 KB; at radius 8
-// the split ring needs 36-48 KB. 8-row tiles (128 threads, 23-45 KB): five
+// resident blocks per SM. 16-row tiles: three 256-thread blocks, registers
+// capped at 80 per thread; at radius 4 the forward modes need 73 KB of shared
+// memory, the split-ring backward modes 54 KB; at radius 8 the split ring
+// needs 36-48 KB. 8-row tiles (128 threads): five blocks at radius 4 (102
+// registers, 17-29 KB), four at radius 8 (128 registers, 4-point vectors,
+// 30-53 KB)
 template <int R, int MODE, int BY = 16>
 constexpr int tma_min_blocks() {
-    return BY == 16 ? 3 : 5;
+    return BY == 16 ? 3 : (R == 8 ? 4 : 5);
 }
 // the rings of the resident blocks fit the SM's 228 KB (1 KB reserved per block)
 template <int R, int MODE, int BY = 16>
@@ -257,7 +261,7 @@ constexpr bool rings_fit() {
 template <int R, int MODE, int BY>
 __global__ void __launch_bounds__(16 * BY, (tma_min_blocks<R, MODE, BY>()))
     k_stencil_tma(const __grid_constant__ StepArgs A, const __grid_constant__ TmaMaps M, int* status) {
-    constexpr int V = points_per_thread<R>();
+    constexpr int V = points_per_thread<R, BY>();
     using T = TmaTile<R, V, BY>;
     using VT = Vec<V>;
     using C = TmaCfg<R, MODE, BY>;
@@ -331,7 +335,7 @@ __global__ void __launch_bounds__(16 * BY, (tma_min_blocks<R, MODE, BY>()))
     }
     // queue planes zb - R .. zb + R - 1 straight from global memory
     // queue: plane z0 + t of a group reads entries t .. t + 2r (head 2r + t)
-    constexpr int G = queue_group<R>();
+    constexpr int G = queue_group<R, V>();
     VT q[2 * R + G];
 #pragma unroll
     for (int i = 0; i < 2 * R; i++) {
@@ -529,7 +533,7 @@ cudaError_t make_map(CUtensorMap* m, const float* base, int nx, int ny, int nz, 
 
 template <int R, int MODE, int BY>
 cudaError_t launch_tma_t(const StepArgs& a, int* status, cudaStream_t s) {
-    using T = TmaTile<R, points_per_thread<R>(), BY>;
+    using T = TmaTile<R, points_per_thread<R, BY>(), BY>;
     constexpr int smem = TmaCfg<R, MODE, BY>::SMEM;
     static_assert(rings_fit<R, MODE, BY>(), "rings do not fit the resident blocks");
     static bool attr = false;
