@@ -591,7 +591,9 @@ def batch_leg(args, dev):
                         ckpt_every=args.batch_ckpt)
     budget = 200 * 10 ** 9
     tuned = None
-    if not args.no_autotune:  # tile rows x slab height, timed on an 8-step run
+    if args.variant:  # a given kernel variant, automatic slabs
+        rtm.set_tuning(p.radius, 0, args.variant)
+    elif not args.no_autotune:  # tile rows x slab height, timed on an 8-step run
         from paper_1603_03971_gb300 import autotune
 
         tuned = autotune.tune_batch(p, aps, vel, nt=8, budget=budget)
@@ -619,6 +621,7 @@ def batch_leg(args, dev):
                         % (shots, nt, args.batch_ckpt),
             "seconds": t, "gpoint_updates_per_s": updates / t / 1e9, "updates": updates,
             "workspace_gb": ws.numel() / 1e9,
+            "variant": args.variant or (tuned["variant"] if tuned else 0),
             "tuning": None if tuned is None else {
                 "tile_rows": 8 if tuned["variant"] == 3 else 16, "zchunk": tuned["zchunk"],
                 "trials_ms": tuned["trials"]}}
