@@ -80,9 +80,9 @@ def tune_stencil(radius: int, padded_shape: Tuple[int, int, int], steps: int = 1
                  cache_path: str = CACHE, force: bool = False,
                  variants: Tuple[int, ...] = (1, 2, 3)) -> dict:
     """Best plane-load path and tile (1 vector loads; 2 TMA, 16-row tiles; 3
-    TMA, 8-row tiles) and z-slab height for the single-shot stencil on a
-    padded grid (NZ, NY, NX), timed on a constant-velocity model; trials are
-    keyed "variant/zchunk"."""
+    TMA, 8-row tiles of 4-point vectors) and z-slab height for the
+    single-shot stencil on a padded grid (NZ, NY, NX), timed on a
+    constant-velocity model; trials are keyed "variant/zchunk"."""
     from . import RtmError, alloc_workspace, make_params, model_prep, set_tuning
 
     key = _key("stencil", radius, padded_shape)
