@@ -1,0 +1,54 @@
+"""Host logic of bench.py (no GPU): the ncu traffic figure of the committed
+profile is reported only for the kernel source, radius, tile rows and padded
+grid it was measured on."""
+import hashlib
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "..")
+sys.path.insert(0, ROOT)
+bench = pytest.importorskip("bench")
+
+
+def _profile(tmp_path, src_bytes, radius=4, rows=8, grid="576x576x576", traffic=4870143166):
+    src = tmp_path / "stencil.cu"
+    src.write_bytes(src_bytes)
+    prof = tmp_path / "profile.md"
+    prof.write_text("# summary\n\nradius: %d\ntile_rows: %d\npadded_grid: %s\n"
+                    "traffic_bytes_per_launch: %d\nstencil_source_sha256: %s\n"
+                    % (radius, rows, grid, traffic, hashlib.sha256(src_bytes).hexdigest()))
+    return str(src), str(prof)
+
+
+def test_traffic_matches_only_the_profiled_launch(tmp_path, monkeypatch):
+    src, prof = _profile(tmp_path, b"kernel source A")
+    monkeypatch.setattr(bench, "STENCIL_SRC", src)
+    monkeypatch.setattr(bench, "PROFILE", prof)
+    assert bench.profiled_traffic(4, 8, (576, 576, 576)) == 4870143166
+    assert bench.profiled_traffic(8, 8, (576, 576, 576)) is None  # other radius
+    assert bench.profiled_traffic(4, 16, (576, 576, 576)) is None  # other tile
+    assert bench.profiled_traffic(4, 8, (448, 448, 448)) is None  # other grid
+    with open(src, "wb") as f:  # the kernel changed since the capture
+        f.write(b"kernel source B")
+    assert bench.profiled_traffic(4, 8, (576, 576, 576)) is None
+
+
+def test_missing_or_incomplete_profile(tmp_path, monkeypatch):
+    src, prof = _profile(tmp_path, b"k")
+    monkeypatch.setattr(bench, "STENCIL_SRC", src)
+    monkeypatch.setattr(bench, "PROFILE", str(tmp_path / "absent.md"))
+    assert bench.profiled_traffic(4, 8, (576, 576, 576)) is None
+    text = open(prof).read().replace("tile_rows: 8\n", "")
+    with open(prof, "w") as f:
+        f.write(text)
+    monkeypatch.setattr(bench, "PROFILE", prof)
+    assert bench.profiled_traffic(4, 8, (576, 576, 576)) is None
+
+
+def test_committed_profile_names_its_launch():
+    text = open(bench.PROFILE).read()
+    for key in ("radius:", "tile_rows:", "padded_grid:", "traffic_bytes_per_launch:",
+                "stencil_source_sha256:"):
+        assert key in text
