@@ -361,6 +361,25 @@ def learned_leg(args, dev):
     from paper_1603_03971_gb300 import codec
 
     enc_ms, dec_ms = codec._time_codec(w.nx, reps=10)
+    # bf16 tensor-core work per snapshot as executed: E1 (2^3 patch, K padded
+    # to 16) and E2 (3^3 x 32 taps); D1 (k4 s2: 2^3 taps x 16 channels per
+    # output) and D2 (32 channels -> 2^3 outputs, N padded to 16)
+    h, q = (w.nx // 2) ** 3, (w.nx // 4) ** 3
+    enc_flop = 2 * h * 32 * 16 + 2 * q * 16 * 32 * 27
+    dec_flop = 2 * h * 32 * 16 * 8 + 2 * h * 32 * 16
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16 = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    codec_tc = {
+        "encode_gflop": enc_flop / 1e9, "decode_gflop": dec_flop / 1e9,
+        "encode_tflops": enc_flop / (enc_ms * 1e-3) / 1e12,
+        "decode_tflops": dec_flop / (dec_ms * 1e-3) / 1e12,
+        "peak_tflops": bf16,
+        "peak_kind": "measured sustained bf16" if "bf16_tflops_sustained" in peaks
+        else "fallback sustained bf16",
+    }
+    codec_tc["encode_frac"] = codec_tc["encode_tflops"] / bf16
+    codec_tc["decode_frac"] = codec_tc["decode_tflops"] / bf16
     err = float((img_l - img_c).norm() / img_c.norm())
     err_deep = float((img_l[16:] - img_c[16:]).norm() / img_c[16:].norm())
     NZ, NY, NX = w.padded_shape
@@ -377,6 +396,7 @@ def learned_leg(args, dev):
         "image_rel_l2_vs_checkpoint": err, "target_rel_l2": 1e-2,
         "image_rel_l2_below_z16": err_deep,
         "codec_ms_per_snapshot": {"encode": enc_ms, "decode": dec_ms},
+        "codec_tensor": codec_tc,
         "compression": "8x (float32 snapshot -> 16 bfloat16 channels per 4^3 voxels)",
         "train": {"models": args.learned_models, "snapshots": n_snap,
                   "steps": args.learned_train_steps, "batch": 4, "seconds": train_s,
