@@ -73,7 +73,7 @@ class Case:
                               self.src, self.receivers(), squared=squared)
 
 
-class GpuRun:
+class DeviceShot:
     """Device buffers of one case and the calls through the C ABI."""
 
     def __init__(self, case: Case, want_grad=False, device="cuda", vel=None, squared=False):

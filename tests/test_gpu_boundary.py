@@ -7,7 +7,7 @@ sponge, thin models, ragged tiles) hold."""
 import numpy as np
 import pytest
 
-from helpers import Case, GpuRun, rel_l2
+from helpers import Case, DeviceShot, rel_l2
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
@@ -26,7 +26,7 @@ def _reset_tuning():
 
 
 def _image(case, d_obs=None):
-    g = GpuRun(case)
+    g = DeviceShot(case)
     g.forward()
     if d_obs is None:
         d_obs = case.d_obs(g.nrec)
@@ -83,7 +83,7 @@ def test_shot_and_illumination():
     import paper_1603_03971_gb300 as rtm
 
     case = Case(storage="boundary", r=4, nt=48, image_every=2, **SMALL)
-    g = GpuRun(case)
+    g = DeviceShot(case)
     d_obs = case.d_obs(g.nrec)
     dd = torch.from_numpy(np.ascontiguousarray(d_obs, dtype=np.float32)).cuda()
     img = torch.zeros((case.nz, case.ny, case.nx), device="cuda")

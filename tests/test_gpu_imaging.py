@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import rtm_inputs
-from helpers import Case, GpuRun, rel_l2
+from helpers import Case, DeviceShot, rel_l2
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
@@ -33,7 +33,7 @@ def test_illumination_matches_oracle(r, storage, ck, ie, shape):
     from oracle import imaging
 
     case = Case(r=r, nt=48, storage=storage, ckpt_every=ck, image_every=ie, **shape)
-    g = GpuRun(case)
+    g = DeviceShot(case)
     g.forward()
     d_obs = case.d_obs(g.nrec)
     img, illum = _illum_run(g, d_obs)
@@ -63,7 +63,7 @@ def test_illumination_in_learned_storage_is_that_of_the_decoded_snapshots():
     case = Case(r=4, nt=40, storage="learned", image_every=ie, nx=32, ny=24, nz=20, nb=6)
     P = rtm_inputs.ae_flat(rtm_inputs.ae_init_params(2)).astype(np.float32)
     Pd = torch.from_numpy(P).cuda()
-    g = GpuRun(case)
+    g = DeviceShot(case)
     rtm.forward_learned(g.p, g.c, g.rec, Pd, g.ws)
     rtm.check(g.ws)
     d_obs = case.d_obs(g.nrec)

@@ -45,13 +45,13 @@ def test_learned_shot_matches_the_oracle_chain(window):
     (recomputed), the later ones coded."""
     import torch
 
-    from helpers import GpuRun
+    from helpers import DeviceShot
     from oracle import ae as oae
 
     ie = 4
     case = Case(nx=32, ny=28, nz=24, nb=8, r=4, nt=40, image_every=ie)
     P = rtm_inputs.ae_flat(rtm_inputs.ae_init_params(2)).astype(np.float32)
-    g = GpuRun(case)
+    g = DeviceShot(case)
     d_obs = case.d_obs(g.nrec)
     img = _learned_image(case, g, torch.from_numpy(P).cuda(), d_obs, window)
     # oracle: snapshots, codec and imaging, all on the CPU
@@ -73,11 +73,11 @@ def test_learned_shot_matches_the_oracle_chain(window):
 def test_exact_window_over_the_whole_run_is_the_store_all_image():
     import torch
 
-    from helpers import GpuRun
+    from helpers import DeviceShot
 
     case = Case(nx=32, ny=28, nz=24, nb=8, r=4, nt=40, image_every=4)
     P = torch.from_numpy(rtm_inputs.ae_flat(rtm_inputs.ae_init_params(2)).astype(np.float32)).cuda()
-    g = GpuRun(case)
+    g = DeviceShot(case)
     d_obs = case.d_obs(g.nrec)
     img = _learned_image(case, g, P, d_obs, window=case.nt)
     g.forward()
@@ -92,7 +92,7 @@ def test_trained_codec_beats_the_untrained_network():
     correspondingly closer to the store-all image."""
     import torch
 
-    from helpers import GpuRun
+    from helpers import DeviceShot
     from oracle import ae as oae
     import paper_1603_03971_gb300 as rtm
     from paper_1603_03971_gb300 import codec, learned
@@ -106,7 +106,7 @@ def test_trained_codec_beats_the_untrained_network():
     ie = 8
     case = Case(nx=n, ny=n, nz=n, nb=16, r=4, nt=480, image_every=ie, f0=20.0, t0=0.05,
                 vmax=4500.0, src=(48, 40, 4), rec_stride=3, seed=77, sigma=8.0)
-    g = GpuRun(case)
+    g = DeviceShot(case)
     g.forward()
     exact = {m: rtm.snapshot(g.p, g.ws, m).clone() for m in range(ie, case.nt + 1, ie)}
     d_obs = case.d_obs(g.nrec)

@@ -4,7 +4,7 @@ data, images and gradients; FP32 fields against FP64)."""
 import numpy as np
 import pytest
 
-from helpers import Case, GpuRun, rel_l2
+from helpers import Case, DeviceShot, rel_l2
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
@@ -31,7 +31,7 @@ def test_model_prep_matches_oracle():
     import oracle
 
     case = Case(**SHAPES["ragged"])
-    g = GpuRun(case)
+    g = DeviceShot(case)
     c_ref = oracle.model_c(case.velocity(), case.nb, case.dt)
     c = g.c.cpu().numpy()
     assert c.shape == c_ref.shape
@@ -49,7 +49,7 @@ def test_forward_parity(r, shape, zchunk):
     if shape == "thin":
         case.rec_stride = 1
     rtm.set_tuning(r, zchunk, 0)
-    g = GpuRun(case)
+    g = DeviceShot(case)
     data, last = g.forward(keep_last=True)
     ref = case.oracle_problem().forward(keep_last=True)
     assert rel_l2(data.cpu().numpy(), ref["data"]) <= TOL
@@ -61,7 +61,7 @@ def test_forward_parity(r, shape, zchunk):
 @pytest.mark.parametrize("storage,ck", [("all", 0), ("ckpt", 16), ("ckpt", 7)])
 def test_backward_image_parity(r, storage, ck):
     case = Case(r=r, nt=60, storage=storage, ckpt_every=ck, **SHAPES["ragged"])
-    g = GpuRun(case)
+    g = DeviceShot(case)
     g.forward()
     d_obs = case.d_obs(g.nrec)
     img, adj = g.backward_image(d_obs, src_adj=True)
@@ -79,7 +79,7 @@ def test_checkpointing_reproduces_store_all_exactly():
     imgs = []
     for storage, ck in (("all", 0), ("ckpt", 10), ("ckpt", 45), ("ckpt", 1)):
         case = Case(storage=storage, ckpt_every=ck, **base)
-        g = GpuRun(case)
+        g = DeviceShot(case)
         g.forward()
         img, _ = g.backward_image(case.d_obs(g.nrec))
         imgs.append(img.cpu().numpy())
@@ -90,7 +90,7 @@ def test_checkpointing_reproduces_store_all_exactly():
 @pytest.mark.parametrize("storage,ck", [("all", 0), ("ckpt", 12)])
 def test_image_every_fourth_step(storage, ck):
     case = Case(r=4, nt=50, storage=storage, ckpt_every=ck, image_every=4, **SHAPES["small"])
-    g = GpuRun(case)
+    g = DeviceShot(case)
     g.forward()
     d_obs = case.d_obs(g.nrec)
     img, _ = g.backward_image(d_obs)
@@ -107,7 +107,7 @@ def test_dot_product_on_gpu(r):
     import oracle
 
     case = Case(r=r, nt=60, **SHAPES["small"])
-    g = GpuRun(case)
+    g = DeviceShot(case)
     data, _ = g.forward()
     q = case.d_obs(g.nrec)
     _, adj = g.backward_image(q, src_adj=True)
@@ -120,7 +120,7 @@ def test_dot_product_on_gpu(r):
 def test_source_and_receivers_in_the_sponge():
     extra = np.array([[-3, 4, 5], [31, -2, 3], [5, 6, -4], [0, 0, 25]], np.int32)
     case = Case(r=4, nt=50, src=(-2, 9, 4), extra_rec=extra, **SHAPES["small"])
-    g = GpuRun(case)
+    g = DeviceShot(case)
     data, _ = g.forward()
     d_obs = case.d_obs(g.nrec)
     img, adj = g.backward_image(d_obs, src_adj=True)
@@ -133,7 +133,7 @@ def test_source_and_receivers_in_the_sponge():
 
 def test_no_sponge_and_single_step():
     case = Case(r=4, nt=1, nb=0, nx=32, ny=20, nz=12, src=(5, 6, 7))
-    g = GpuRun(case)
+    g = DeviceShot(case)
     data, last = g.forward(keep_last=True)
     ref = case.oracle_problem().forward(keep_last=True)
     assert rel_l2(last[1].cpu().numpy(), ref["last"][1]) <= TOL
@@ -164,7 +164,7 @@ def test_receiver_out_of_range_is_flagged_not_faulted():
 
     extra = np.array([[500, 0, 0]], np.int32)
     case = Case(r=4, nt=10, extra_rec=extra, **SHAPES["small"])
-    g = GpuRun(case)
+    g = DeviceShot(case)
     import torch
 
     data = torch.empty((case.nt, g.nrec), device="cuda")
@@ -206,7 +206,7 @@ def test_cfl_and_bad_models_are_rejected():
 @pytest.mark.parametrize("r,storage,ck", [(4, "all", 0), (4, "ckpt", 9), (8, "ckpt", 16)])
 def test_gradient_parity(r, storage, ck):
     case = Case(r=r, nt=50, storage=storage, ckpt_every=ck, **SHAPES["small"])
-    g = GpuRun(case, want_grad=True, squared=True)
+    g = DeviceShot(case, want_grad=True, squared=True)
     g.forward()
     resid = case.d_obs(g.nrec)
     grad = g.grad(resid).cpu().numpy()
@@ -242,11 +242,11 @@ def test_autograd_function_and_central_differences():
     import rtm_inputs
 
     case = Case(r=4, nt=60, storage="ckpt", ckpt_every=16, **SHAPES["small"])
-    g = GpuRun(case, want_grad=True, squared=True)
+    g = DeviceShot(case, want_grad=True, squared=True)
     p = g.p
     v2 = g.vel.clone()
     blob = rtm_inputs.blob_perturbation(np.sqrt(case.velocity()), 0.05, 4.0) ** 2
-    gobs = GpuRun(case, want_grad=True, vel=blob, squared=True)
+    gobs = DeviceShot(case, want_grad=True, vel=blob, squared=True)
     d_obs, _ = gobs.forward()
     x = v2.clone().requires_grad_(True)
     J = rtm.RtmMisfit.apply(x, p, g.rec, d_obs, g.ws)
@@ -277,7 +277,7 @@ def test_shot_host_matches_device_path():
     img_h = torch.empty((case.nz, case.ny, case.nx), dtype=torch.float32).pin_memory()
     rtm.shot_host(p, torch.from_numpy(v).pin_memory(), torch.from_numpy(rec).pin_memory(),
                   torch.from_numpy(d_obs).pin_memory(), img_h, ws_h)
-    g = GpuRun(case)
+    g = DeviceShot(case)
     img = torch.zeros((case.nz, case.ny, case.nx), device="cuda")
     rtm.shot(p, g.c, g.rec, torch.from_numpy(d_obs).cuda(), g.ws, img)
     np.testing.assert_array_equal(img_h.numpy(), img.cpu().numpy())

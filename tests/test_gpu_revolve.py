@@ -4,7 +4,7 @@ match the oracle, for zero to many slots and imaging every k steps."""
 import numpy as np
 import pytest
 
-from helpers import Case, GpuRun, rel_l2
+from helpers import Case, DeviceShot, rel_l2
 
 pytestmark = pytest.mark.gpu
 SMALL = dict(nx=28, ny=24, nz=20, nb=6)
@@ -19,12 +19,12 @@ def test_revolve_equals_store_all_and_the_oracle(slots, ie, nt, r, shape):
 
     base = dict(r=r, nt=nt, image_every=ie, **shape)
     ca = Case(storage="all", **base)
-    ga = GpuRun(ca)
+    ga = DeviceShot(ca)
     ga.forward()
     d_obs = ca.d_obs(ga.nrec)
     img_a, adj_a = ga.backward_image(d_obs, src_adj=True)
     cr = Case(storage="revolve", ckpt_every=slots, **base)
-    gr = GpuRun(cr)
+    gr = DeviceShot(cr)
     gr.forward()
     img_r, adj_r = gr.backward_image(d_obs, src_adj=True)
     assert torch.equal(img_r, img_a)
@@ -44,13 +44,13 @@ def test_revolve_shot_and_workspace():
 
     base = dict(r=4, nt=60, image_every=1, **SMALL)
     ca = Case(storage="all", **base)
-    ga = GpuRun(ca)
+    ga = DeviceShot(ca)
     d_obs = ca.d_obs(ga.nrec)
     dd = torch.from_numpy(np.ascontiguousarray(d_obs, dtype=np.float32)).cuda()
     img_a = torch.zeros((ca.nz, ca.ny, ca.nx), device="cuda")
     rtm.shot(ga.p, ga.c, ga.rec, dd, ga.ws, img_a)
     cr = Case(storage="revolve", ckpt_every=4, **base)
-    gr = GpuRun(cr)
+    gr = DeviceShot(cr)
     img_r = torch.zeros_like(img_a)
     rtm.shot(gr.p, gr.c, gr.rec, dd, gr.ws, img_r)
     rtm.check(gr.ws)

@@ -4,7 +4,7 @@ z slabs shorter than the stencil radius, in all five kernel modes."""
 import numpy as np
 import pytest
 
-from helpers import Case, GpuRun, rel_l2
+from helpers import Case, DeviceShot, rel_l2
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
@@ -40,7 +40,7 @@ def test_tma_forward_parity(r, shape, zchunk, variant):
     if shape == "thin":
         case.rec_stride = 1
     _use(r, zchunk, variant)
-    g = GpuRun(case)
+    g = DeviceShot(case)
     data, last = g.forward(keep_last=True)
     ref = case.oracle_problem().forward(keep_last=True)
     assert rel_l2(data.cpu().numpy(), ref["data"]) <= TOL
@@ -52,7 +52,7 @@ def test_tma_forward_parity(r, shape, zchunk, variant):
 def test_tma_backward_image_parity(r, storage, ck, variant):
     case = Case(r=r, nt=50, storage=storage, ckpt_every=ck, **SHAPES["ragged"])
     _use(r, 0, variant)
-    g = GpuRun(case)
+    g = DeviceShot(case)
     g.forward()
     d_obs = case.d_obs(g.nrec)
     img, adj = g.backward_image(d_obs, src_adj=True)
@@ -67,7 +67,7 @@ def test_tma_backward_image_parity(r, storage, ck, variant):
 def test_tma_gradient_parity(variant):
     case = Case(r=4, nt=40, storage="ckpt", ckpt_every=9, **SHAPES["small"])
     _use(4, 0, variant)
-    g = GpuRun(case, want_grad=True, squared=True)
+    g = DeviceShot(case, want_grad=True, squared=True)
     g.forward()
     resid = case.d_obs(g.nrec)
     grad = g.grad(resid).cpu().numpy()
@@ -84,7 +84,7 @@ def test_tma_agrees_with_vector_loads():
     out = []
     for variant in (1, 2, 3):
         rtm.set_tuning(4, 0, variant)
-        g = GpuRun(case)
+        g = DeviceShot(case)
         data, last = g.forward(keep_last=True)
         out.append(last.cpu().numpy())
     assert rel_l2(out[1], out[0]) <= 1e-6

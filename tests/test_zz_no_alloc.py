@@ -12,7 +12,7 @@ import ctypes
 import numpy as np
 import pytest
 
-from helpers import Case, GpuRun, rel_l2
+from helpers import Case, DeviceShot, rel_l2
 
 TOL = 1e-4
 
@@ -33,7 +33,7 @@ def test_noalloc_forward_matches_workspace_forward_twice():
     import torch
 
     case = Case(r=4, nt=60, nx=100, ny=44, nz=37, nb=10)
-    g = GpuRun(case)
+    g = DeviceShot(case)
     data_ref, last_ref = g.forward(keep_last=True)
     for call in range(2):
         data = torch.full_like(data_ref, float("nan"))
