@@ -217,10 +217,10 @@ size_t rtm_host_workspace_size(const rtm_params *p);
 /* One RTM shot from HOST buffers, end to end: copies h_vel [nz][ny][nx],
  * h_rec [nrec][3] and h_dobs [nt][nrec] to the device workspace, prepares the
  * model, runs the shot and copies the image [nz][ny][nx] back into h_image
- * (overwritten). The observed data are copied on a private stream while the
- * model is prepared and the source is propagated; the receiver pass waits
- * for them. Pinned host memory makes the copies asynchronous. Returns after
- * the stream has been synchronised. */
+ * (overwritten). The observed data are copied on a private stream after the
+ * velocity and receivers, while the model is prepared and the source is
+ * propagated; the receiver pass waits for them. Pinned host memory makes
+ * the copies asynchronous. Returns after the stream has been synchronised. */
 rtm_status rtm_shot_host(const rtm_params *p, const float *h_vel, int32_t vel_kind,
                          const int32_t *h_rec, const float *h_dobs, float *h_image,
                          void *d_ws, size_t ws_bytes, rtm_stream stream);

@@ -1092,26 +1092,35 @@ rtm_status rtm_shot_host(const rtm_params* p, const float* h_vel, int32_t vel_ki
     off += up(sizeof(float) * (size_t)p->nt * p->nrec);
     float* img = reinterpret_cast<float*>(base + off);
     // the observed data are read only by the receiver pass: they travel on a
-    // side stream while the model is prepared and the source is propagated
+    // side stream while the model is prepared and the source is propagated.
+    // That copy starts after the velocity and receiver uploads: two
+    // host-to-device copies at once ran far below the rate of one, and
+    // slower with every repetition, while one copy beside the kernels keeps
+    // the full rate
     struct Side {
         cudaStream_t st = nullptr;
-        cudaEvent_t ev = nullptr;
+        cudaEvent_t up = nullptr;  // velocity and receivers uploaded
+        cudaEvent_t ev = nullptr;  // observed data uploaded
         ~Side() {
             if (st) cudaStreamSynchronize(st);
             if (ev) cudaEventDestroy(ev);
+            if (up) cudaEventDestroy(up);
             if (st) cudaStreamDestroy(st);
         }
     } side;
     CU(cudaStreamCreateWithFlags(&side.st, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&side.up, cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&side.ev, cudaEventDisableTiming));
-    if (p->nrec > 0)
-        CU(cudaMemcpyAsync(dobs, h_dobs, sizeof(float) * (size_t)p->nt * p->nrec,
-                           cudaMemcpyHostToDevice, side.st));
-    CU(cudaEventRecord(side.ev, side.st));
     CU(cudaMemcpyAsync(vel, h_vel, sizeof(float) * d.nmodel, cudaMemcpyHostToDevice, s));
     if (p->nrec > 0)
         CU(cudaMemcpyAsync(rec, h_rec, sizeof(int32_t) * 3 * (size_t)p->nrec,
                            cudaMemcpyHostToDevice, s));
+    CU(cudaEventRecord(side.up, s));
+    CU(cudaStreamWaitEvent(side.st, side.up, 0));
+    if (p->nrec > 0)
+        CU(cudaMemcpyAsync(dobs, h_dobs, sizeof(float) * (size_t)p->nt * p->nrec,
+                           cudaMemcpyHostToDevice, side.st));
+    CU(cudaEventRecord(side.ev, side.st));
     CHECK(rtm_model_prep(p, vel, vel_kind, c, d_ws, ws_bytes, stream));
     CU(cudaMemsetAsync(img, 0, sizeof(float) * d.nmodel, s));
     CHECK(rtm_forward(p, c, rec, nullptr, d_ws, ws_bytes, nullptr, stream));
