@@ -1,9 +1,11 @@
-// Stencil step with TMA plane loads (tuning variant 2).
+// Stencil step with TMA plane loads (tuning variants 2 and 3).
 //
 // The same leapfrog update and epilogues as k_stencil, with the plane loads
-// moved to the tensor memory accelerator. A 256-thread block owns a tile of
-// x-y columns (64 x 16 at radius 4, four points per thread; 32 x 16 at
-// radius 8, two points per thread) and marches a z slab. One thread issues
+// moved to the tensor memory accelerator. A block owns a tile of x-y columns
+// and marches a z slab. Variant 2: 256-thread blocks, 64 x 16 tiles at
+// radius 4 (four points per thread) and 32 x 16 at radius 8 (two points per
+// thread). Variant 3: 128-thread blocks, 64 x 8 tiles with four points per
+// thread at both radii. One thread issues
 // 3D bulk tensor copies of the next planes into shared-memory rings, P
 // planes ahead of the one being computed, each slot completed on its
 // mbarrier by the copy's transaction bytes (expect-tx):

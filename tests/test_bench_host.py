@@ -1,7 +1,6 @@
 """Host logic of bench.py (no GPU): the ncu traffic figure of the committed
-profile is reported only for the kernel source, radius, tile rows and padded
-grid it was measured on."""
-import hashlib
+profile is reported only for the kernel code, radius, tile rows and padded
+grid it was measured on; comments do not count as code."""
 import os
 import sys
 
@@ -17,8 +16,8 @@ def _profile(tmp_path, src_bytes, radius=4, rows=8, grid="576x576x576", traffic=
     src.write_bytes(src_bytes)
     prof = tmp_path / "profile.md"
     prof.write_text("# summary\n\nradius: %d\ntile_rows: %d\npadded_grid: %s\n"
-                    "traffic_bytes_per_launch: %d\nstencil_source_sha256: %s\n"
-                    % (radius, rows, grid, traffic, hashlib.sha256(src_bytes).hexdigest()))
+                    "traffic_bytes_per_launch: %d\nstencil_code_sha256: %s\n"
+                    % (radius, rows, grid, traffic, bench.kernel_code_digest(str(src))))
     return str(src), str(prof)
 
 
@@ -33,6 +32,23 @@ def test_traffic_matches_only_the_profiled_launch(tmp_path, monkeypatch):
     with open(src, "wb") as f:  # the kernel changed since the capture
         f.write(b"kernel source B")
     assert bench.profiled_traffic(4, 8, (576, 576, 576)) is None
+
+
+def test_code_digest_ignores_comments_only(tmp_path):
+    code = 'int f(int a) {\n    const char* s = "a // b /* c */";\n    return a + 1;\n}\n'
+    commented = ('// header\n/* block\n   comment */\nint f(int a) {  // trailing\n\n'
+                 '    const char* s = "a // b /* c */";\n    return a + 1;  /* x */\n}\n')
+    changed = code.replace("a + 1", "a + 2")
+    digests = []
+    for i, text in enumerate((code, commented, changed)):
+        path = tmp_path / ("k%d.cu" % i)
+        path.write_text(text)
+        digests.append(bench.kernel_code_digest(str(path)))
+    assert digests[0] == digests[1]  # comments and blank lines only
+    assert digests[0] != digests[2]  # a code change
+    s_lit = tmp_path / "lit.cu"  # a string literal keeps its "//"
+    s_lit.write_text(code.replace('"a // b /* c */"', '"a"'))
+    assert bench.kernel_code_digest(str(s_lit)) != digests[0]
 
 
 def test_missing_or_incomplete_profile(tmp_path, monkeypatch):
@@ -50,5 +66,5 @@ def test_missing_or_incomplete_profile(tmp_path, monkeypatch):
 def test_committed_profile_names_its_launch():
     text = open(bench.PROFILE).read()
     for key in ("radius:", "tile_rows:", "padded_grid:", "traffic_bytes_per_launch:",
-                "stencil_source_sha256:"):
+                "stencil_code_sha256:"):
         assert key in text
