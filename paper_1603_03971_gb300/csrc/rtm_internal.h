@@ -69,7 +69,7 @@ inline void set_region(StepArgs& a, int mode) {
 }
 
 cudaError_t launch_stencil(int radius, int mode, const StepArgs& a, cudaStream_t s);
-// the same step with TMA plane loads (tuning variant 2); status: device status word
+// the same step with TMA plane loads (tuning variants 2 and 3); status: device status word
 // tile_rows: 16 (256-thread blocks) or 8 (128-thread blocks)
 cudaError_t launch_stencil_tma(int radius, int mode, const StepArgs& a, int* status,
                                cudaStream_t s, int tile_rows = 16);
