@@ -62,7 +62,8 @@ typedef enum {
     RTM_ERR_WORKSPACE = 3,   /* workspace missing, too small or misaligned */
     RTM_ERR_CUDA = 4,        /* a CUDA runtime call failed */
     RTM_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out */
-    RTM_ERR_NUMERIC = 6,     /* non-finite or non-positive model values */
+    RTM_ERR_NUMERIC = 6,     /* non-finite or non-positive model values, or a
+                                run whose fields hold non-finite values */
     RTM_ERR_UNSUPPORTED = 7, /* e.g. a stencil radius other than 4 or 8 */
     RTM_ERR_STATE = 8        /* workspace prepared for another purpose */
 } rtm_status;
@@ -227,7 +228,10 @@ rtm_status rtm_shot_host(const rtm_params *p, const float *h_vel, int32_t vel_ki
 
 /* Synchronise the stream, read and clear the device status word of the
  * workspace: RTM_OK, RTM_ERR_INVALID (a receiver out of range was skipped),
- * RTM_ERR_TIMEOUT (a bounded wait ran out) or RTM_ERR_CUDA. */
+ * RTM_ERR_TIMEOUT (a bounded wait ran out), RTM_ERR_NUMERIC (the post-run
+ * scan found a NaN or an infinity: every forward pass scans its newest
+ * state u^nt, every receiver pass its image or gradient accumulator) or
+ * RTM_ERR_CUDA. The first error recorded wins. */
 rtm_status rtm_check(void *d_ws, size_t ws_bytes, rtm_stream stream);
 
 /* ---- learned snapshot compression (tensor cores) ------------------------
@@ -441,7 +445,11 @@ rtm_status rtm_batch(const rtm_params *p, int32_t nshots, const rtm_aperture *h_
  * threads) race on the array and must be serialised by the caller. It stores
  * no snapshots or checkpoints, so it cannot feed rtm_backward_image; receivers
  * outside the padded grid get zero traces and are not reported (there is no
- * workspace for rtm_check). It does not update rtm_stats. */
+ * workspace for rtm_check). It does not update rtm_stats. It always runs the
+ * 16-byte vector-load stencil kernel (the plane-load variant of
+ * rtm_set_tuning does not apply); the slab height set by rtm_set_tuning does.
+ * A failed CUDA call returns RTM_ERR_CUDA with its message in
+ * rtm_last_error(). */
 rtm_status rtm_forward_noalloc(const rtm_params *p, const float *d_c, const int32_t *d_rec,
                                float *d_data, float *d_u_last, rtm_stream stream);
 
@@ -452,7 +460,8 @@ rtm_status rtm_forward_noalloc(const rtm_params *p, const float *d_c, const int3
  * tiles of 256 threads; 3 = the same with 8-row tiles of 128 threads and
  * 4-point vectors at both radii, five blocks per SM at radius 4, four at
  * radius 8). Applies to later
- * calls on every thread, to every kernel mode on the padded grid; the
+ * calls on every thread, to every kernel mode on the padded grid (the
+ * allocation-free forward call takes the slab height only); the
  * reverse step of boundary storage, which covers the model region, sizes
  * its slabs for that region. The batched multi-shot kernel (rtm_batch)
  * takes its plane-load path and tile from the same variant and its slab

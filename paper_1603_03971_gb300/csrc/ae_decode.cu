@@ -40,6 +40,7 @@
 #include "ae_internal.h"
 #include "tc_gemm.cuh"
 #include "tma_encode.h"
+#include "wait_clock.cuh"
 
 namespace rtm {
 namespace ae {
@@ -99,6 +100,7 @@ __device__ __forceinline__ void bar_arrive(uint64_t* b) {
 // bounded wait; gives up early once another thread has raised the abort flag
 __device__ __forceinline__ bool wait_bar(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
     const uint32_t a = tc::smem_u32(b);
+    const unsigned long long t0 = wait_now();
     for (long long i = 0; i < kLimit; i++) {
         uint32_t done;
         asm volatile(
@@ -110,6 +112,7 @@ __device__ __forceinline__ bool wait_bar(uint64_t* b, uint32_t parity, volatile 
             : "memory");
         if (done) return true;
         if (abort_flag && *abort_flag) return false;
+        if (wait_expired(i, t0)) break;
     }
     if (abort_flag) *abort_flag = 1;
     return false;

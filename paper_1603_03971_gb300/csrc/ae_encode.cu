@@ -50,6 +50,7 @@
 #include "ae_internal.h"
 #include "tc_gemm.cuh"
 #include "tma_encode.h"
+#include "wait_clock.cuh"
 
 namespace rtm {
 namespace ae {
@@ -109,6 +110,7 @@ __device__ __forceinline__ void bar_arrive(uint64_t* b) {
 }
 __device__ __forceinline__ bool wait_bar(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
     const uint32_t a = tc::smem_u32(b);
+    const unsigned long long t0 = wait_now();
     for (long long i = 0; i < kLimit; i++) {
         uint32_t done;
         asm volatile(
@@ -120,6 +122,7 @@ __device__ __forceinline__ bool wait_bar(uint64_t* b, uint32_t parity, volatile 
             : "memory");
         if (done) return true;
         if (abort_flag && *abort_flag) return false;
+        if (wait_expired(i, t0)) break;
     }
     if (abort_flag) *abort_flag = 1;
     return false;

@@ -301,6 +301,26 @@ __global__ void k_misfit(const float* __restrict__ d, const float* __restrict__ 
     }
 }
 
+// any non-finite value among n floats sets the status word to
+// RTM_ERR_NUMERIC (6); 16-byte loads when the base is aligned
+__global__ void k_finite_scan(const float* __restrict__ f, long long n, int vec, int* status) {
+    bool bad = false;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (vec) {
+        const long long n4 = n / 4;
+        const float4* f4 = reinterpret_cast<const float4*>(f);
+        for (long long i = t; i < n4; i += stride) {
+            const float4 v = __ldcs(f4 + i);
+            bad |= !isfinite(v.x) || !isfinite(v.y) || !isfinite(v.z) || !isfinite(v.w);
+        }
+        for (long long i = 4 * n4 + t; i < n; i += stride) bad |= !isfinite(f[i]);
+    } else {
+        for (long long i = t; i < n; i += stride) bad |= !isfinite(__ldcs(f + i));
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) flag(status, 6);
+}
+
 int grid_for(long long n, int block) {
     long long g = (n + block - 1) / block;
     if (g > 152 * 16) g = 152 * 16;
@@ -399,6 +419,13 @@ cudaError_t launch_grad_finalize(const Geometry& G, const float* acc, const floa
                                  double dx3, double dt2, float* grad_v2, cudaStream_t s) {
     const long long n = (long long)G.nx * G.ny * G.nz;
     k_grad_finalize<<<grid_for(n, 256), 256, 0, s>>>(G, acc, c, dx3, dt2, grad_v2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finite_scan(const float* f, long long n, int* status, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int vec = reinterpret_cast<uintptr_t>(f) % 16 == 0;
+    k_finite_scan<<<grid_for(vec ? n / 4 + 1 : n, 256), 256, 0, s>>>(f, n, vec, status);
     return cudaGetLastError();
 }
 

@@ -67,20 +67,6 @@ struct Plan {
     size_t off_ctrl, off_phases, off_desc, off_wav, off_pool, total;
 };
 
-void weights_b(int r, double* a) {
-    double fr = 1.0;
-    for (int i = 2; i <= r; i++) fr *= i;
-    double sum = 0.0;
-    for (int k = 1; k <= r; k++) {
-        double f1 = 1.0, f2 = 1.0;
-        for (int i = 2; i <= r - k; i++) f1 *= i;
-        for (int i = 2; i <= r + k; i++) f2 *= i;
-        a[k] = 2.0 * ((k % 2 == 1) ? 1.0 : -1.0) * fr * fr / ((double)k * k * f1 * f2);
-        sum += a[k];
-    }
-    a[0] = -2.0 * sum;
-}
-
 rtm_status check_batch(const rtm_params* p, int nshots, const rtm_aperture* sh) {
     rtm_params q = *p;
     q.storage = RTM_STORE_CKPT;
@@ -301,11 +287,7 @@ rtm_status rtm_batch(const rtm_params* p, int32_t nshots, const rtm_aperture* h_
     BatchArgs A;
     memset(&A, 0, sizeof A);
     std::unique_ptr<BatchTmaArgs> T(tma ? new BatchTmaArgs() : nullptr);
-    double a[kMaxRadius + 1];
-    weights_b(p->radius, a);
-    const double inv_dx2 = 1.0 / (p->dx * p->dx);
-    A.a[0] = (float)(3.0 * a[0] * inv_dx2);
-    for (int k = 1; k <= p->radius; k++) A.a[k] = (float)(a[k] * inv_dx2);
+    step_weights(p->radius, p->dx, A.a);
     A.inv_dx3 = (float)(1.0 / (p->dx * p->dx * p->dx));
     A.phases = reinterpret_cast<const BatchPhase*>(ws + P.off_phases);
     A.nphases = (int)P.phases.size();

@@ -25,6 +25,7 @@
 #include "batch_internal.h"
 #include "packed_f32x2.cuh"
 #include "tma_encode.h"
+#include "wait_clock.cuh"
 
 namespace rtm {
 
@@ -107,6 +108,7 @@ __device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
 // or if another block already aborted
 __device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, BatchCtrl* ctrl) {
     const uint32_t a = s_u32(b);
+    const unsigned long long t0 = wait_now();
     for (long long i = 0; i < kPlaneWaitLimit; i++) {
         uint32_t done;
         asm volatile(
@@ -118,6 +120,7 @@ __device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, BatchCtrl
             : "memory");
         if (done) return true;
         if ((i & 1023) == 1023 && *reinterpret_cast<volatile int*>(&ctrl->abort)) return false;
+        if (wait_expired(i, t0)) break;
     }
     atomicExch(&ctrl->abort, 1);
     atomicCAS(&ctrl->status, 0, 5);  // RTM_ERR_TIMEOUT
@@ -127,6 +130,7 @@ __device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, BatchCtrl
 // flight land before an aborting block leaves
 __device__ __forceinline__ void bar_drain(uint64_t* b, uint32_t parity) {
     const uint32_t a = s_u32(b);
+    const unsigned long long t0 = wait_now();
     for (long long i = 0; i < kPlaneWaitLimit; i++) {
         uint32_t done;
         asm volatile(
@@ -136,7 +140,7 @@ __device__ __forceinline__ void bar_drain(uint64_t* b, uint32_t parity) {
             : "=r"(done)
             : "r"(a), "r"(parity)
             : "memory");
-        if (done) return;
+        if (done || wait_expired(i, t0)) return;
     }
 }
 __device__ __forceinline__ void bar_arrive(uint64_t* b) {

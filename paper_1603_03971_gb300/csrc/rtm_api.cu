@@ -46,28 +46,10 @@ rtm_status fail(rtm_status st, const char* fmt, ...) {
         if (s_ != RTM_OK) return s_;         \
     } while (0)
 
-// ---- stencil weights (closed form) -------------------------------------------
-// a_k = 2 (-1)^(k+1) (r!)^2 / (k^2 (r-k)! (r+k)!), a_0 = -2 sum_k a_k: the
-// centred 2r-order second-derivative weights.
-void weights(int r, double* a) {
-    double fr = 1.0;
-    for (int i = 2; i <= r; i++) fr *= i;
-    double sum = 0.0;
-    for (int k = 1; k <= r; k++) {
-        double f_rmk = 1.0, f_rpk = 1.0;
-        for (int i = 2; i <= r - k; i++) f_rmk *= i;
-        for (int i = 2; i <= r + k; i++) f_rpk *= i;
-        const double sign = (k % 2 == 1) ? 1.0 : -1.0;
-        a[k] = 2.0 * sign * fr * fr / ((double)k * k * f_rmk * f_rpk);
-        sum += a[k];
-    }
-    a[0] = -2.0 * sum;
-}
-
 // largest stable vmax dt / dx: 2 / sqrt(3 |S(pi)|), S(pi) = a0 + 2 sum (-1)^k a_k
 double stability_limit(int r) {
     double a[kMaxRadius + 1];
-    weights(r, a);
+    stencil_weights(r, a);
     double s = a[0];
     for (int k = 1; k <= r; k++) s += 2.0 * ((k % 2) ? -a[k] : a[k]);
     return 2.0 / sqrt(3.0 * fabs(s));
@@ -347,12 +329,8 @@ rtm_status make_ctx(Ctx& C, const rtm_params* p, const float* c, void* ws, rtm_s
     C.src = ((long long)(p->src_z + p->nb) * C.d.NY + (p->src_y + p->nb)) * C.d.NX +
             (p->src_x + p->nb);
     C.inv_dx3 = (float)(1.0 / (p->dx * p->dx * p->dx));
-    double a[kMaxRadius + 1];
-    weights(p->radius, a);
     memset(&C.base, 0, sizeof C.base);
-    const double inv_dx2 = 1.0 / (p->dx * p->dx);
-    C.base.a[0] = (float)(3.0 * a[0] * inv_dx2);
-    for (int k = 1; k <= p->radius; k++) C.base.a[k] = (float)(a[k] * inv_dx2);
+    step_weights(p->radius, p->dx, C.base.a);
     C.base.c = c;
     C.base.gx = C.at(C.L.gx);
     C.base.gy = C.at(C.L.gy);
@@ -522,6 +500,10 @@ rtm_status run_forward(Ctx& C, const int32_t* rec, float* data, float* u_last) {
         CU(cudaMemcpyAsync(u_last, prev, fb, cudaMemcpyDeviceToDevice, C.s));
         CU(cudaMemcpyAsync(u_last + C.d.N, cur, fb, cudaMemcpyDeviceToDevice, C.s));
     }
+    // a non-finite value, once it appears, stays in the newest state: one
+    // scan of u^{nt} flags a run that blew up (rtm_check reports it)
+    CU(launch_finite_scan(cur, (long long)C.d.N, C.status(), C.s));
+    count_launch();
     return RTM_OK;
 }
 
@@ -732,6 +714,9 @@ rtm_status run_backward(Ctx& C, const int32_t* rec, const float* rdata, float* s
     }
     // n = 0 terms: source trace and gradient source term of mu^1
     CHECK(bwd_aux(C, mcur, mprev, rec, nullptr, src_adj, grad ? acc : nullptr, C.wav()));
+    // post-run scan of the accumulated image or gradient
+    CU(launch_finite_scan(acc, (long long)(grad ? C.d.N : C.d.slab), C.status(), C.s));
+    count_launch();
     return RTM_OK;
 }
 
@@ -756,6 +741,36 @@ rtm_status common_checks(const rtm_params* p, const float* d_c, const int32_t* d
 }
 
 }  // namespace
+
+// ---- stencil weights (closed form) -------------------------------------------
+void rtm::stencil_weights(int r, double* a) {
+    double fr = 1.0;
+    for (int i = 2; i <= r; i++) fr *= i;
+    double sum = 0.0;
+    for (int k = 1; k <= r; k++) {
+        double f_rmk = 1.0, f_rpk = 1.0;
+        for (int i = 2; i <= r - k; i++) f_rmk *= i;
+        for (int i = 2; i <= r + k; i++) f_rpk *= i;
+        const double sign = (k % 2 == 1) ? 1.0 : -1.0;
+        a[k] = 2.0 * sign * fr * fr / ((double)k * k * f_rmk * f_rpk);
+        sum += a[k];
+    }
+    a[0] = -2.0 * sum;
+}
+
+void rtm::step_weights(int r, double dx, float* out) {
+    double a[kMaxRadius + 1];
+    stencil_weights(r, a);
+    const double inv_dx2 = 1.0 / (dx * dx);
+    out[0] = (float)(3.0 * a[0] * inv_dx2);
+    for (int k = 1; k <= r; k++) out[k] = (float)(a[k] * inv_dx2);
+}
+
+int rtm::tuning_zchunk(int radius) {
+    if (radius < 0 || radius > kMaxRadius) return 0;
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_zchunk[radius];
+}
 
 int rtm::tuning_variant(int radius) {
     if (radius < 0 || radius > kMaxRadius) return 0;
@@ -1009,12 +1024,8 @@ rtm_status rtm_image_filter(const rtm_params* p, const float* d_image, const flo
     if (d_laplacian) {
         LapWeights w;
         memset(&w, 0, sizeof w);
-        double a[kMaxRadius + 1];
-        weights(p->radius, a);
-        const double inv_dx2 = 1.0 / (p->dx * p->dx);
         w.r = p->radius;
-        w.a[0] = (float)(3.0 * a[0] * inv_dx2);
-        for (int k = 1; k <= p->radius; k++) w.a[k] = (float)(a[k] * inv_dx2);
+        step_weights(p->radius, p->dx, w.a);
         CU(launch_image_laplacian(d_image, p->nx, p->ny, p->nz, w, d_laplacian, s));
         count_launch();
     }
@@ -1142,6 +1153,8 @@ rtm_status rtm_check(void* d_ws, size_t ws_bytes, rtm_stream stream) {
     CU(cudaStreamSynchronize(s));
     if (h == RTM_ERR_INVALID) return fail(RTM_ERR_INVALID, "a receiver lies outside the padded grid");
     if (h == RTM_ERR_TIMEOUT) return fail(RTM_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (h == RTM_ERR_NUMERIC)
+        return fail(RTM_ERR_NUMERIC, "a wavefield, image or gradient holds non-finite values");
     if (h != 0) return fail((rtm_status)h, "device status %d", h);
     return RTM_OK;
 }

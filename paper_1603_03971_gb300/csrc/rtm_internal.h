@@ -26,6 +26,13 @@ enum StencilMode : int {
 
 constexpr int kMaxRadius = 8;
 
+// Centred 2r-order second-derivative weights (closed form, rtm_api.cu):
+// a_k = 2 (-1)^(k+1) (r!)^2 / (k^2 (r-k)! (r+k)!), a_0 = -2 sum_k a_k.
+void stencil_weights(int r, double* a);
+// The stencil kernels' coefficients from those weights: a[0] = 3 a_0 / dx^2
+// (the centre term of the three axes), a[k] = a_k / dx^2; a has r + 1 entries.
+void step_weights(int r, double dx, float* a);
+
 // Arguments of one stencil launch. The "slab" layout used by imaging
 // snapshots and the internal image is [nz][ny][NX]: z and y restricted to the
 // model region, x over the full padded row, so that it shares the 16-byte
@@ -107,6 +114,9 @@ cudaError_t launch_grad_finalize(const Geometry& G, const float* acc, const floa
                                  double dx3, double dt2, float* grad_v2, cudaStream_t s);
 cudaError_t launch_misfit(const float* d, const float* obs, long long n, float* resid,
                           double* J, cudaStream_t s);
+// post-run check: any non-finite value among n floats sets *status to
+// RTM_ERR_NUMERIC (unless another error is already recorded)
+cudaError_t launch_finite_scan(const float* f, long long n, int* status, cudaStream_t s);
 // imaging-condition variants: source illumination (+= u^2 of a snapshot
 // slab's model columns), illumination-normalised image, Laplacian filter
 struct LapWeights {
@@ -130,5 +140,7 @@ cudaError_t launch_image_laplacian(const float* image, int nx, int ny, int nz,
 int set_error(int code, const char* fmt, ...);
 // plane-load variant chosen by rtm_set_tuning for a radius (0: automatic)
 int tuning_variant(int radius);
+// z-slab height chosen by rtm_set_tuning for a radius (0: automatic)
+int tuning_zchunk(int radius);
 
 }  // namespace rtm

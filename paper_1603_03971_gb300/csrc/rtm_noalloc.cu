@@ -35,6 +35,15 @@ void* g_na_ptr[kMaxDevices] = {nullptr};
 
 size_t up_na(size_t v) { return (v + kAlignNA - 1) / kAlignNA * kAlignNA; }
 
+// a failed CUDA call returns RTM_ERR_CUDA with its message in rtm_last_error()
+#define NA_CU(call)                                                                    \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return (rtm_status)set_error(RTM_ERR_CUDA, "rtm_forward_noalloc: %s failed: %s", \
+                                         #call, cudaGetErrorString(e_));               \
+    } while (0)
+
 // The scratch's device address on the current device, looked up once per device.
 cudaError_t scratch_address(void** out) {
     int dev = 0;
@@ -50,21 +59,6 @@ cudaError_t scratch_address(void** out) {
     }
     *out = g_na_ptr[dev];
     return cudaSuccess;
-}
-
-// centred 2r-order second-derivative weights (closed form)
-void weights_na(int r, double* a) {
-    double fr = 1.0;
-    for (int i = 2; i <= r; i++) fr *= i;
-    double sum = 0.0;
-    for (int k = 1; k <= r; k++) {
-        double f_rmk = 1.0, f_rpk = 1.0;
-        for (int i = 2; i <= r - k; i++) f_rmk *= i;
-        for (int i = 2; i <= r + k; i++) f_rpk *= i;
-        a[k] = 2.0 * ((k % 2 == 1) ? 1.0 : -1.0) * fr * fr / ((double)k * k * f_rmk * f_rpk);
-        sum += a[k];
-    }
-    a[0] = -2.0 * sum;
 }
 
 }  // namespace
@@ -99,6 +93,7 @@ extern "C" rtm_status rtm_forward_noalloc(const rtm_params* p, const float* d_c,
             "scratch holds %zu; use rtm_forward with a workspace",
             need, NX, NY, NZ, (size_t)kNoAllocBytes);
 
+    cudaGetLastError();  // a stale error of the caller's earlier work is not ours
     void* base = nullptr;
     cudaError_t ea = scratch_address(&base);
     if (ea != cudaSuccess)
@@ -115,21 +110,17 @@ extern "C" rtm_status rtm_forward_noalloc(const rtm_params* p, const float* d_c,
     float* cur = reinterpret_cast<float*>(s8 + o_f1);
 
     // the array keeps the previous call's contents: clear what starts at zero
-    if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return RTM_ERR_CUDA;
-    if (cudaMemsetAsync(prev, 0, sizeof(float) * N, s) != cudaSuccess) return RTM_ERR_CUDA;
-    if (cudaMemsetAsync(cur, 0, sizeof(float) * N, s) != cudaSuccess) return RTM_ERR_CUDA;
+    NA_CU(cudaMemsetAsync(status, 0, sizeof(int), s));
+    NA_CU(cudaMemsetAsync(prev, 0, sizeof(float) * N, s));
+    NA_CU(cudaMemsetAsync(cur, 0, sizeof(float) * N, s));
 
     Geometry G{NX, NY, NZ, p->nb, p->nx, p->ny, p->nz};
-    if (launch_wavelet(p->nt, p->dt, p->f0, p->t0, wav, s) != cudaSuccess) return RTM_ERR_CUDA;
-    if (launch_sponge(G, gx, gy, gz, s) != cudaSuccess) return RTM_ERR_CUDA;
+    NA_CU(launch_wavelet(p->nt, p->dt, p->f0, p->t0, wav, s));
+    NA_CU(launch_sponge(G, gx, gy, gz, s));
 
     StepArgs A;
     memset(&A, 0, sizeof A);
-    double a[kMaxRadius + 1];
-    weights_na(p->radius, a);
-    const double inv_dx2 = 1.0 / (p->dx * p->dx);
-    A.a[0] = (float)(3.0 * a[0] * inv_dx2);
-    for (int k = 1; k <= p->radius; k++) A.a[k] = (float)(a[k] * inv_dx2);
+    step_weights(p->radius, p->dx, A.a);
     A.c = d_c;
     A.gx = gx;
     A.gy = gy;
@@ -141,7 +132,10 @@ extern "C" rtm_status rtm_forward_noalloc(const rtm_params* p, const float* d_c,
     A.nx = p->nx;
     A.ny = p->ny;
     A.nz = p->nz;
-    A.zchunk = auto_zchunk(p->radius, NX, NY, NZ);
+    // the slab height set by rtm_set_tuning applies; the plane loads are
+    // always the vector-load kernel's
+    const int zc = tuning_zchunk(p->radius);
+    A.zchunk = zc > 0 ? zc : auto_zchunk(p->radius, NX, NY, NZ);
     if ((NZ + A.zchunk - 1) / A.zchunk > 65535) A.zchunk = (NZ + 65534) / 65535;
     set_region(A, MODE_FWD);
 
@@ -150,27 +144,22 @@ extern "C" rtm_status rtm_forward_noalloc(const rtm_params* p, const float* d_c,
     const float inv_dx3 = (float)(1.0 / (p->dx * p->dx * p->dx));
     for (int n = 0; n < p->nt; n++) {
         float* row = (d_data && n >= 1) ? d_data + (size_t)(n - 1) * p->nrec : nullptr;
-        if (launch_fwd_aux(G, cur, prev, d_c, gx, gy, gz, d_rec, p->nrec, row, src, wav + n,
-                           inv_dx3, status, s) != cudaSuccess)
-            return RTM_ERR_CUDA;
+        NA_CU(launch_fwd_aux(G, cur, prev, d_c, gx, gy, gz, d_rec, p->nrec, row, src, wav + n,
+                             inv_dx3, status, s));
         A.u_cur = cur;
         A.u_prev = prev;
-        if (launch_stencil(p->radius, MODE_FWD, A, s) != cudaSuccess) return RTM_ERR_CUDA;
+        NA_CU(launch_stencil(p->radius, MODE_FWD, A, s));
         float* t = prev;
         prev = cur;
         cur = t;
     }
-    if (d_data &&
-        launch_fwd_aux(G, cur, prev, d_c, gx, gy, gz, d_rec, p->nrec,
-                       d_data + (size_t)(p->nt - 1) * p->nrec, src, nullptr, inv_dx3, status,
-                       s) != cudaSuccess)
-        return RTM_ERR_CUDA;
+    if (d_data)
+        NA_CU(launch_fwd_aux(G, cur, prev, d_c, gx, gy, gz, d_rec, p->nrec,
+                             d_data + (size_t)(p->nt - 1) * p->nrec, src, nullptr, inv_dx3,
+                             status, s));
     if (d_u_last) {
-        if (cudaMemcpyAsync(d_u_last, prev, sizeof(float) * N, cudaMemcpyDeviceToDevice, s) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(d_u_last + N, cur, sizeof(float) * N, cudaMemcpyDeviceToDevice, s) !=
-                cudaSuccess)
-            return RTM_ERR_CUDA;
+        NA_CU(cudaMemcpyAsync(d_u_last, prev, sizeof(float) * N, cudaMemcpyDeviceToDevice, s));
+        NA_CU(cudaMemcpyAsync(d_u_last + N, cur, sizeof(float) * N, cudaMemcpyDeviceToDevice, s));
     }
     return RTM_OK;
 }

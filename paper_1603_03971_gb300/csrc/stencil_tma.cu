@@ -35,9 +35,11 @@
 
 #include <mutex>
 
+#include "packed_f32x2.cuh"
 #include "rtm_internal.h"
 #include "stencil_common.cuh"
 #include "tma_encode.h"
+#include "wait_clock.cuh"
 
 namespace rtm {
 
@@ -119,32 +121,6 @@ __device__ __forceinline__ void vst_stream(float* p, const Vec<V>& a) {
         __stcs(reinterpret_cast<float2*>(p), make_float2(a.v[0], a.v[1]));
 }
 
-// packed fp32 pairs (sm_100 family f32x2 arithmetic: IEEE single precision
-// per lane, two lanes per instruction)
-__device__ __forceinline__ uint64_t pk2(float a, float b) {
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk2(uint64_t r, float& a, float& b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
-    uint64_t r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
-    uint64_t r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
-    uint64_t r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-
 // the Laplacian on packed pairs of points, with half the floating-point
 // instructions. Radius 4 keeps the scalar form's order of sums (two point
 // pairs per thread already give two independent chains); radius 8 (one pair
@@ -217,22 +193,37 @@ __device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(b)), "r"(bytes)
                  : "memory");
 }
+__device__ __forceinline__ bool bar_poll(uint32_t a, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// bounded wait (poll count and elapsed time); false if it ran out (then the
+// block's abort flag is raised) or if the block already aborted
 __device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, int* abort_flag) {
     if (*reinterpret_cast<volatile int*>(abort_flag)) return false;
     const uint32_t a = s_u32(b);
+    const unsigned long long t0 = wait_now();
     for (long long i = 0; i < kTmaWaitLimit; i++) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.b32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
+        if (bar_poll(a, parity)) return true;
+        if (wait_expired(i, t0)) break;
     }
     *reinterpret_cast<volatile int*>(abort_flag) = 1;
     return false;
+}
+// bounded wait that ignores the abort flag: lets a copy already in flight
+// land in shared memory before the block leaves
+__device__ __forceinline__ void bar_drain(uint64_t* b, uint32_t parity) {
+    const uint32_t a = s_u32(b);
+    const unsigned long long t0 = wait_now();
+    for (long long i = 0; i < kTmaWaitLimit; i++)
+        if (bar_poll(a, parity) || wait_expired(i, t0)) return;
 }
 __device__ __forceinline__ void tma3(float* dst, const CUtensorMap* map, int x, int y, int z,
                                      uint64_t* bar) {
@@ -301,12 +292,17 @@ __global__ void __launch_bounds__(16 * BY, (tma_min_blocks<R, MODE, BY>()))
     // newest u^n plane copied with its halo: the queue head of the last step
     // (joint ring) or the last centre plane (split ring)
     const int last_u = C::SPLIT ? ze - 1 : ze - 1 + R;
+    // thread 0 issues planes in order: u^n planes [zb, u_end), pointwise
+    // operand planes [zb, a_end)
+    int u_end = zb, a_end = zb;
     auto issue_u = [&](int p) {
+        u_end = p + 1;
         const int slot = (p - zb) % C::SU;
         bar_expect(&ubar[slot], C::UPLANE * 4);
         tma3(uring + slot * C::UPLANE, &M.u, x0 - R, y0 - R, p, &ubar[slot]);
     };
     auto issue_a = [&](int p) {
+        a_end = p + 1;
         const int slot = (p - zb) % C::SA;
         float* base = aring + slot * C::NAH * C::APLANE;
         bar_expect(&abar[slot], C::NAH * C::APLANE * 4);
@@ -394,38 +390,38 @@ __global__ void __launch_bounds__(16 * BY, (tma_min_blocks<R, MODE, BY>()))
             VT lap;
             if constexpr (packed_math<R>()) {
                 uint64_t L2[V / 2], L2o[V / 2];
-                const uint64_t a0 = pk2(A.a[0], A.a[0]);
+                const uint64_t a0 = f32x2::pack(A.a[0], A.a[0]);
 #pragma unroll
                 for (int j = 0; j < V / 2; j++) {
-                    L2[j] = mul2(a0, pk2(q[R + t].v[2 * j], q[R + t].v[2 * j + 1]));
+                    L2[j] = f32x2::mul(a0, f32x2::pack(q[R + t].v[2 * j], q[R + t].v[2 * j + 1]));
                     L2o[j] = 0;  // the bit pattern of two +0.0f
                 }
 #pragma unroll
                 for (int k = 1; k <= R; k++) {
                     const VT ym_ = vlds<V>(S + (R + ty - k) * T::SW + R + V * tx);
                     const VT yp_ = vlds<V>(S + (R + ty + k) * T::SW + R + V * tx);
-                    const uint64_t ak = pk2(A.a[k], A.a[k]);
+                    const uint64_t ak = f32x2::pack(A.a[k], A.a[k]);
 #pragma unroll
                     for (int j = 0; j < V / 2; j++) {
                         const int i = 2 * j;
-                        const uint64_t px = add2(pk2(v[R + i - k], v[R + i + 1 - k]),
-                                                 pk2(v[R + i + k], v[R + i + 1 + k]));
-                        const uint64_t py = add2(pk2(ym_.v[i], ym_.v[i + 1]),
-                                                 pk2(yp_.v[i], yp_.v[i + 1]));
-                        const uint64_t pz = add2(pk2(q[R + t - k].v[i], q[R + t - k].v[i + 1]),
-                                                 pk2(q[R + t + k].v[i], q[R + t + k].v[i + 1]));
+                        const uint64_t px = f32x2::add(f32x2::pack(v[R + i - k], v[R + i + 1 - k]),
+                                                 f32x2::pack(v[R + i + k], v[R + i + 1 + k]));
+                        const uint64_t py = f32x2::add(f32x2::pack(ym_.v[i], ym_.v[i + 1]),
+                                                 f32x2::pack(yp_.v[i], yp_.v[i + 1]));
+                        const uint64_t pz = f32x2::add(f32x2::pack(q[R + t - k].v[i], q[R + t - k].v[i + 1]),
+                                                 f32x2::pack(q[R + t + k].v[i], q[R + t + k].v[i + 1]));
                         if (split_chains<R>() && (k & 1))
-                            L2o[j] = fma2(ak, add2(add2(px, py), pz), L2o[j]);
+                            L2o[j] = f32x2::fma(ak, f32x2::add(f32x2::add(px, py), pz), L2o[j]);
                         else
-                            L2[j] = fma2(ak, add2(add2(px, py), pz), L2[j]);
+                            L2[j] = f32x2::fma(ak, f32x2::add(f32x2::add(px, py), pz), L2[j]);
                     }
                 }
 #pragma unroll
                 for (int j = 0; j < V / 2; j++) {
                     if constexpr (split_chains<R>())
-                        upk2(add2(L2[j], L2o[j]), lap.v[2 * j], lap.v[2 * j + 1]);
+                        f32x2::unpack(f32x2::add(L2[j], L2o[j]), lap.v[2 * j], lap.v[2 * j + 1]);
                     else
-                        upk2(L2[j], lap.v[2 * j], lap.v[2 * j + 1]);
+                        f32x2::unpack(L2[j], lap.v[2 * j], lap.v[2 * j + 1]);
                 }
             } else {
 #pragma unroll
@@ -509,17 +505,76 @@ __global__ void __launch_bounds__(16 * BY, (tma_min_blocks<R, MODE, BY>()))
         for (int o = 16; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
         if ((tid & 31) == 0 && ssq != 0.f) atomicAdd(A.sumsq, (double)ssq);
     }
-    // a slab shorter than r issued planes [ze, zb + r) that no step waited
-    // for: let those copies land before the block exits
+    // every copy must land before the block exits: a slab shorter than r
+    // issued planes [ze, zb + r) that no step waited for, and after an abort
+    // the remaining waits returned at once. The newest plane issued into each
+    // slot is the only one that can still be in flight (an earlier one was
+    // waited for before its slot was refilled), so wait for it, bounded and
+    // ignoring the abort flag; a completed phase answers at once
     if (tid == 0) {
-        for (int p = ze; p < zb + R && p <= last_u; p++)
-            bar_wait(&ubar[(p - zb) % C::SU], (uint32_t)(((p - zb) / C::SU) & 1), &abort_flag);
+        for (int s = 0; s < C::SU; s++) {
+            const int j = u_end - 1 - zb;
+            if (j < s) break;
+            const int jl = s + (j - s) / C::SU * C::SU;
+            bar_drain(&ubar[s], (uint32_t)((jl / C::SU) & 1));
+        }
+        for (int s = 0; s < C::SA; s++) {
+            const int j = a_end - 1 - zb;
+            if (j < s) break;
+            const int jl = s + (j - s) / C::SA * C::SA;
+            bar_drain(&abar[s], (uint32_t)((jl / C::SA) & 1));
+        }
         if (abort_flag && status) atomicCAS(status, 0, 5);  // RTM_ERR_TIMEOUT
     }
 }
 
 // ---- host side: tensor maps ---------------------------------------------------
+cudaError_t encode_map(CUtensorMap* m, const float* base, int nx, int ny, int nz, int bx,
+                       int by);
+
+// A shot launches the stencil thousands of times on the same few buffers, so
+// the encoded maps are kept per thread, keyed by every encoding argument, and
+// reused (least recently encoded entry replaced)
+struct MapKey {
+    const float* base;
+    int nx, ny, nz, bx, by;
+    bool operator==(const MapKey& o) const {
+        return base == o.base && nx == o.nx && ny == o.ny && nz == o.nz && bx == o.bx &&
+               by == o.by;
+    }
+};
+constexpr int kMapCache = 64;
+struct MapCache {
+    MapKey key[kMapCache];
+    CUtensorMap map[kMapCache];
+    int n = 0, next = 0;
+};
+thread_local MapCache t_maps;
+
 cudaError_t make_map(CUtensorMap* m, const float* base, int nx, int ny, int nz, int bx, int by) {
+    const MapKey k{base, nx, ny, nz, bx, by};
+    MapCache& c = t_maps;
+    for (int i = 0; i < c.n; i++)
+        if (c.key[i] == k) {
+            *m = c.map[i];
+            return cudaSuccess;
+        }
+    cudaError_t e = encode_map(m, base, nx, ny, nz, bx, by);
+    if (e != cudaSuccess) return e;
+    int slot;
+    if (c.n < kMapCache) {
+        slot = c.n++;
+    } else {
+        slot = c.next;
+        c.next = (c.next + 1) % kMapCache;
+    }
+    c.key[slot] = k;
+    c.map[slot] = *m;
+    return cudaSuccess;
+}
+
+cudaError_t encode_map(CUtensorMap* m, const float* base, int nx, int ny, int nz, int bx,
+                       int by) {
     EncodeTiledFn f = tma_encoder();
     if (!f) return cudaErrorNotSupported;
     if (((uintptr_t)base % 16) || (nx % 4)) return cudaErrorInvalidValue;

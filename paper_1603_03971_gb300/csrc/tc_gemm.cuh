@@ -26,6 +26,7 @@
 #include <stdint.h>
 
 #include <type_traits>
+#include "wait_clock.cuh"
 
 namespace rtm {
 namespace tc {
@@ -104,6 +105,7 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
 // bounded wait for the completion of the phase with the given parity
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     const uint32_t a = smem_u32(bar);
+    const unsigned long long t0 = wait_now();
     for (long long i = 0; i < kWaitLimit; i++) {
         uint32_t done;
         asm volatile(
@@ -114,6 +116,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
+        if (wait_expired(i, t0)) break;
     }
     return false;
 }
