@@ -197,3 +197,85 @@ def test_batch_at_full_size_matches_single_shots():
         del w
     assert float(ref.abs().max()) > 0
     assert rel_l2(img.cpu().numpy(), ref.cpu().numpy()) <= TOL
+
+
+_FULL_ORACLE = {}
+
+
+def test_batch_at_full_size_matches_the_oracle_on_real_apertures():
+    """The batched-shots workload at its full size, in its launch
+    configuration: all 32 seeded apertures of the 1024 x 1024 x 512 layered /
+    salt model in one batch (radius 8, checkpoints every 10, 30 steps), and
+    two of its real apertures (160 x 160 x 288 and 160 x 256 x 288) against
+    the FP64 oracle run on each whole aperture: at radius 8 the stencil's
+    reach after 30 steps (240 cells) spans the aperture, so the exact crop is
+    the aperture itself. The modelled data of those two shots are compared
+    directly; the other shots get zero observed data, so the image is the
+    sum of the two shots' images."""
+    import torch
+
+    import oracle
+    import paper_1603_03971_gb300 as rtm
+    from paper_1603_03971_gb300 import batch
+
+    cfg = rtm_inputs.BATCH_WORKLOAD
+    nz, ny, nx = cfg["model_shape"]
+    nt, k, nb, r = 30, 10, cfg["nb"], cfg["radius"]
+    vel_np = rtm_inputs.layered_salt_velocity(nx, ny, nz, seed=cfg["seed"])
+    origin, size = rtm_inputs.batch_apertures(cfg["nshots"], (nz, ny, nx), seed=cfg["seed"])
+    aps = [batch.Aperture(int(o[0]), int(o[1]), int(o[2]), int(s[0]), int(s[1]), int(s[2]),
+                          int(s[0]) // 2, int(s[1]) // 2, 4, 2) for o, s in zip(origin, size)]
+    picked = [15, 18]
+    dt = rtm_inputs.courant_dt(cfg["dx"], cfg["vmax"])
+    p = rtm.make_params(nx, ny, nz, nb, r, nt, cfg["dx"], dt, cfg["f0"], 1.0 / cfg["f0"],
+                        (0, 0, 0), 0, storage="ckpt", ckpt_every=k)
+    dobs = [rtm_inputs.standard_normal((nt, a.ny, a.nx), seed=120 + i).astype(np.float32) * 1e-3
+            if i in picked else np.zeros((nt, a.ny, a.nx), np.float32)
+            for i, a in enumerate(aps)]
+    vel = torch.from_numpy(vel_np).cuda()
+    d = torch.from_numpy(np.concatenate([x.ravel() for x in dobs])).cuda()
+    data = torch.zeros_like(d)
+    img = torch.zeros((nz, ny, nx), device="cuda")
+    ws = batch.alloc_workspace(p, aps)
+    batch.run(p, aps, vel, d, img, ws, data=data)
+    rtm.check(ws)
+    del ws
+    offs = np.cumsum([0] + [nt * a.nx * a.ny for a in aps])
+    data_np = data.cpu().numpy()
+    if not _FULL_ORACLE:
+        for i in picked:
+            a = aps[i]
+            v = vel_np[a.oz:a.oz + a.nz, a.oy:a.oy + a.ny, a.ox:a.ox + a.nx].astype(np.float64)
+            rec = rtm_inputs.surface_receivers(a.nx, a.ny, a.rec_z)
+            prob = oracle.Problem(v, nb, r, cfg["dx"], dt, nt, cfg["f0"], 1.0 / cfg["f0"],
+                                  (a.src_x, a.src_y, a.src_z), rec)
+            fw = prob.forward(keep_u=True)
+            bw = prob.grid.adjoint(prob.w, prob.src, prob.rec,
+                                   dobs[i].reshape(nt, -1).astype(np.float64), snap_u=fw["u"])
+            _FULL_ORACLE[i] = (fw["data"], bw["image"])
+            del fw, bw, prob
+    ref_img = {}
+    for i in picked:
+        a = aps[i]
+        ref_data, img_i = _FULL_ORACLE[i]
+        got = data_np[offs[i]:offs[i + 1]].reshape(nt, -1)
+        assert rel_l2(got, ref_data) <= TOL, i
+        ref_img[i] = img_i
+    # the image: the two shots' images summed over their (overlapping) apertures
+    boxes = [(aps[i], ref_img[i]) for i in picked]
+    z0 = min(a.oz for a, _ in boxes)
+    z1 = max(a.oz + a.nz for a, _ in boxes)
+    y0 = min(a.oy for a, _ in boxes)
+    y1 = max(a.oy + a.ny for a, _ in boxes)
+    x0 = min(a.ox for a, _ in boxes)
+    x1 = max(a.ox + a.nx for a, _ in boxes)
+    ref = np.zeros((z1 - z0, y1 - y0, x1 - x0))
+    for a, im in boxes:
+        ref[a.oz - z0:a.oz - z0 + a.nz, a.oy - y0:a.oy - y0 + a.ny,
+            a.ox - x0:a.ox - x0 + a.nx] += im
+    got = img[z0:z1, y0:y1, x0:x1].cpu().numpy()
+    assert np.abs(ref).max() > 0
+    assert rel_l2(got, ref) <= TOL
+    # nothing outside the two apertures
+    tot = float(img.abs().sum())
+    assert tot == pytest.approx(float(np.abs(got).sum()), rel=1e-6)

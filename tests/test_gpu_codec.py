@@ -228,3 +228,43 @@ def test_adam_step_matches_oracle():
     ref = {"w": P0.astype(np.float32).astype(np.float64)}
     oae.adam_step(ref, {"w": g}, {}, 1, lr=1e-3, clip=1.0)
     np.testing.assert_allclose(P.cpu().numpy(), ref["w"], rtol=1e-5, atol=1e-7)
+
+
+@pytest.mark.parametrize("shape", [(160, 96, 72), (48, 72, 136)])
+def test_marching_codec_matches_oracle_at_full_scheduling_size(shape):
+    """The z-marching encoder and decoder that the learned RTM shot runs,
+    each against the FP64 oracle, element by element, at sizes that reach
+    their full scheduling paths: several latent columns in x and y with
+    ragged last columns (72 -> 18 and 136 -> 34 latent x points against
+    16-point columns; 96 -> 24 and 72 -> 18 latent y points against 8-row
+    columns) and several z chunks per column."""
+    import torch
+
+    from oracle import ae as oae
+    from paper_1603_03971_gb300 import codec
+
+    nz, ny, nx = shape
+    P = _params(8)
+    s = rtm_inputs.standard_normal(shape, 63, np.float32)
+    s[:, :, nx // 3:] *= 2.5  # a scale jump across columns
+    Pd = _cuda(P)
+    ws = codec.alloc_workspace(shape)
+    try:
+        codec.set_encoder("march")
+        codec.set_decoder("march")
+        lat, sc = codec.encode(Pd, _cuda(s), ws)
+        out = codec.decode(Pd, lat, sc, ws)
+        torch.cuda.synchronize()
+    finally:
+        codec.set_encoder("auto")
+        codec.set_decoder("auto")
+    import paper_1603_03971_gb300 as rtm
+
+    rtm.check(ws)
+    params = oae.unflatten(P)
+    lat_or, sc_or = oae.encode(params, s.astype(np.float64))
+    assert float(sc.item()) == pytest.approx(sc_or, rel=1e-6)
+    assert rel_l2(lat.float().cpu().numpy(), lat_or) <= TOL
+    # the decoder on the GPU's latent, on both sides
+    ref = oae.decode(params, lat.float().cpu().numpy().astype(np.float64), float(sc.item()))
+    assert rel_l2(out.cpu().numpy(), ref) <= TOL
