@@ -69,7 +69,7 @@ typedef enum {
 } rtm_status;
 
 enum { RTM_STORE_ALL = 0, RTM_STORE_CKPT = 1, RTM_STORE_LEARNED = 2, RTM_STORE_REVOLVE = 3,
-       RTM_STORE_BOUNDARY = 4 };
+       RTM_STORE_BOUNDARY = 4, RTM_STORE_DECIMATED = 5 };
 enum { RTM_VEL_V = 0, RTM_VEL_V2 = 1 };
 
 typedef struct {
@@ -92,13 +92,23 @@ typedef struct {
                                RTM_STORE_BOUNDARY: the model region's boundary
                                band of every state, the source wavefield
                                recovered by reverse time stepping (imaging
-                               only; model sides above 2 radius) */
+                               only; model sides above 2 radius);
+                               RTM_STORE_DECIMATED: the non-learned 8x scheme
+                               beside learned storage: every other model
+                               sample per axis of each imaging snapshot, kept
+                               in float32 ([(nz+1)/2][(ny+1)/2][(nx+1)/2]) and
+                               rebuilt by linear interpolation along each
+                               axis (the last odd sample copies its left
+                               neighbour) before the imaging step (imaging
+                               only; rtm_forward / rtm_backward_image /
+                               rtm_shot) */
     int32_t ckpt_every;     /* steps per checkpoint segment (RTM_STORE_CKPT);
                                number of checkpoint slots (RTM_STORE_REVOLVE);
-                               exact window (RTM_STORE_LEARNED): the imaging
-                               snapshots of steps 1..ckpt_every are recomputed
-                               from the zero initial state in the backward
-                               call instead of being coded (0: none) */
+                               exact window (RTM_STORE_LEARNED,
+                               RTM_STORE_DECIMATED): the imaging snapshots of
+                               steps 1..ckpt_every are recomputed from the
+                               zero initial state in the backward call
+                               instead of being coded (0: none) */
     int32_t image_every;    /* image at steps m with m % image_every == 0 (>= 1) */
     int32_t want_grad;      /* 1: prepare the workspace for rtm_grad instead of imaging */
 } rtm_params;

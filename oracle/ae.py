@@ -313,11 +313,14 @@ def decimate(s):
     return np.asarray(s, np.float64)[::2, ::2, ::2].astype(np.float32).astype(np.float64)
 
 
-def trilinear_upsample(d, N: int):
+def trilinear_upsample(d, N):
     """Linear interpolation of a decimated field back to N samples per axis
-    (sample 2i holds d[i]; the last odd sample copies its left neighbour)."""
+    (sample 2i holds d[i]; the last odd sample copies its left neighbour).
+    N is one size for all three axes or a (nz, ny, nx) triple."""
     out = np.asarray(d, np.float64)
+    sizes = (N, N, N) if np.isscalar(N) else tuple(N)
     for axis in range(3):
+        N = sizes[axis]
         n = out.shape[axis]
         shape = list(out.shape)
         shape[axis] = N

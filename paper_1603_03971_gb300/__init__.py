@@ -16,8 +16,8 @@ from typing import Optional
 
 import torch
 
-from ._lib import (RTM_STORE_ALL, RTM_STORE_BOUNDARY, RTM_STORE_CKPT, RTM_STORE_LEARNED,
-                   RTM_STORE_REVOLVE, RTM_VEL_V, RTM_VEL_V2,
+from ._lib import (RTM_STORE_ALL, RTM_STORE_BOUNDARY, RTM_STORE_CKPT, RTM_STORE_DECIMATED,
+                   RTM_STORE_LEARNED, RTM_STORE_REVOLVE, RTM_VEL_V, RTM_VEL_V2,
                    RtmError, RtmParams, RtmStats, call, lib)
 
 __all__ = [
@@ -42,7 +42,7 @@ def make_params(nx, ny, nz, nb, radius, nt, dx, dt, f0, t0, src, nrec, storage="
     p.nrec = int(nrec)
     p.storage = {"all": RTM_STORE_ALL, "ckpt": RTM_STORE_CKPT,
                  "learned": RTM_STORE_LEARNED, "revolve": RTM_STORE_REVOLVE,
-                 "boundary": RTM_STORE_BOUNDARY}[storage]
+                 "boundary": RTM_STORE_BOUNDARY, "decimated": RTM_STORE_DECIMATED}[storage]
     p.ckpt_every = int(ckpt_every)
     p.image_every = int(image_every)
     p.want_grad = 1 if want_grad else 0

@@ -16,7 +16,8 @@ STATUS_NAMES = {
     4: "RTM_ERR_CUDA", 5: "RTM_ERR_TIMEOUT", 6: "RTM_ERR_NUMERIC", 7: "RTM_ERR_UNSUPPORTED",
     8: "RTM_ERR_STATE",
 }
-RTM_STORE_ALL, RTM_STORE_CKPT, RTM_STORE_LEARNED, RTM_STORE_REVOLVE, RTM_STORE_BOUNDARY = 0, 1, 2, 3, 4
+(RTM_STORE_ALL, RTM_STORE_CKPT, RTM_STORE_LEARNED, RTM_STORE_REVOLVE, RTM_STORE_BOUNDARY,
+ RTM_STORE_DECIMATED) = 0, 1, 2, 3, 4, 5
 RTM_VEL_V, RTM_VEL_V2 = 0, 1
 
 

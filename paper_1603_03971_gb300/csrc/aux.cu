@@ -321,6 +321,62 @@ __global__ void k_finite_scan(const float* __restrict__ f, long long n, int vec,
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) flag(status, 6);
 }
 
+// decimated storage, coding: keep every other sample of the model region
+// on each axis, coarse[kz][ky][kx] = u[nb + 2 kz][nb + 2 ky][nb + 2 kx] of a
+// padded field; coarse sides are (n + 1) / 2
+__global__ void k_decimate(Geometry G, const float* __restrict__ u, float* __restrict__ coarse,
+                           int cx, int cy, int cz) {
+    const long long n = (long long)cx * cy * cz;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int kx = (int)(i % cx);
+        const int ky = (int)((i / cx) % cy);
+        const int kz = (int)(i / ((long long)cx * cy));
+        coarse[i] = u[((long long)(G.nb + 2 * kz) * G.NY + (G.nb + 2 * ky)) * G.NX + G.nb + 2 * kx];
+    }
+}
+
+// per axis: fine sample j from coarse samples i0 and i0 + 1 with weight w1 on
+// the second: an even sample is a kept one; an odd sample is the mean of its
+// two neighbours, or a copy of the left one past the last kept sample
+__device__ __forceinline__ void lin_axis(int j, int nc, int& i0, float& w1) {
+    i0 = j >> 1;
+    w1 = ((j & 1) && i0 + 1 < nc) ? 0.5f : 0.0f;
+}
+
+// decimated storage, decoding: linear interpolation along each axis back to
+// the model region of a snapshot slab [nz][ny][NX] (columns nb .. nb + nx);
+// the weights (1, 1/2, 1/4, 1/8) are exact, and the corners are summed in a
+// fixed order
+__global__ void k_upsample(Geometry G, const float* __restrict__ coarse, int cx, int cy, int cz,
+                           float* __restrict__ slab) {
+    const long long n = (long long)G.nx * G.ny * G.nz;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int x = (int)(i % G.nx);
+        const int y = (int)((i / G.nx) % G.ny);
+        const int z = (int)(i / ((long long)G.nx * G.ny));
+        int x0, y0, z0;
+        float wx, wy, wz;
+        lin_axis(x, cx, x0, wx);
+        lin_axis(y, cy, y0, wy);
+        lin_axis(z, cz, z0, wz);
+        const int x1 = wx > 0.f ? x0 + 1 : x0, y1 = wy > 0.f ? y0 + 1 : y0,
+                  z1 = wz > 0.f ? z0 + 1 : z0;
+        const float* r00 = coarse + ((long long)z0 * cy + y0) * cx;
+        const float* r01 = coarse + ((long long)z0 * cy + y1) * cx;
+        const float* r10 = coarse + ((long long)z1 * cy + y0) * cx;
+        const float* r11 = coarse + ((long long)z1 * cy + y1) * cx;
+        const float a00 = (1.f - wx) * __ldg(r00 + x0) + wx * __ldg(r00 + x1);
+        const float a01 = (1.f - wx) * __ldg(r01 + x0) + wx * __ldg(r01 + x1);
+        const float a10 = (1.f - wx) * __ldg(r10 + x0) + wx * __ldg(r10 + x1);
+        const float a11 = (1.f - wx) * __ldg(r11 + x0) + wx * __ldg(r11 + x1);
+        const float b0 = (1.f - wy) * a00 + wy * a01;
+        const float b1 = (1.f - wy) * a10 + wy * a11;
+        slab[((long long)z * G.ny + y) * G.NX + G.nb + x] = (1.f - wz) * b0 + wz * b1;
+    }
+}
+
 int grid_for(long long n, int block) {
     long long g = (n + block - 1) / block;
     if (g > 152 * 16) g = 152 * 16;
@@ -426,6 +482,19 @@ cudaError_t launch_finite_scan(const float* f, long long n, int* status, cudaStr
     if (n <= 0) return cudaSuccess;
     const int vec = reinterpret_cast<uintptr_t>(f) % 16 == 0;
     k_finite_scan<<<grid_for(vec ? n / 4 + 1 : n, 256), 256, 0, s>>>(f, n, vec, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decimate(const Geometry& G, const float* u, float* coarse, cudaStream_t s) {
+    const int cx = (G.nx + 1) / 2, cy = (G.ny + 1) / 2, cz = (G.nz + 1) / 2;
+    k_decimate<<<grid_for((long long)cx * cy * cz, 256), 256, 0, s>>>(G, u, coarse, cx, cy, cz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_upsample(const Geometry& G, const float* coarse, float* slab, cudaStream_t s) {
+    const int cx = (G.nx + 1) / 2, cy = (G.ny + 1) / 2, cz = (G.nz + 1) / 2;
+    k_upsample<<<grid_for((long long)G.nx * G.ny * G.nz, 256), 256, 0, s>>>(G, coarse, cx, cy,
+                                                                            cz, slab);
     return cudaGetLastError();
 }
 

@@ -166,7 +166,16 @@ Layout layout_of(const rtm_params* p) {
         L.img = take(sizeof(float) * d.slab);
         L.snap_elems = d.slab;
     }
-    if (p->storage == RTM_STORE_LEARNED) {
+    if (p->storage == RTM_STORE_DECIMATED) {
+        // one float32 coarse snapshot per imaging step, one decode slab plus
+        // the exact window's slabs
+        const size_t nlat = (size_t)(p->nt / p->image_every);
+        L.latent_bytes = up(sizeof(float) * (size_t)((p->nx + 1) / 2) * ((p->ny + 1) / 2) *
+                            ((p->nz + 1) / 2));
+        L.latent = take(L.latent_bytes * (nlat ? nlat : 1));
+        const size_t nwin = (size_t)(p->ckpt_every / p->image_every);
+        L.nsnap = nwin > 1 ? nwin : 1;
+    } else if (p->storage == RTM_STORE_LEARNED) {
         const size_t nlat = (size_t)(p->nt / p->image_every);
         L.latent_bytes = up((size_t)(p->nx / 4) * (p->ny / 4) * (p->nz / 4) * 16 * 2);
         L.latent = take(L.latent_bytes * (nlat ? nlat : 1));
@@ -230,7 +239,7 @@ rtm_status validate(const rtm_params* p) {
     if (p->nrec < 0) return fail(RTM_ERR_INVALID, "nrec %d < 0", p->nrec);
     if (p->storage != RTM_STORE_ALL && p->storage != RTM_STORE_CKPT &&
         p->storage != RTM_STORE_LEARNED && p->storage != RTM_STORE_REVOLVE &&
-        p->storage != RTM_STORE_BOUNDARY)
+        p->storage != RTM_STORE_BOUNDARY && p->storage != RTM_STORE_DECIMATED)
         return fail(RTM_ERR_INVALID, "storage %d unknown", p->storage);
     if (p->storage == RTM_STORE_BOUNDARY) {
         if (p->want_grad)
@@ -257,6 +266,12 @@ rtm_status validate(const rtm_params* p) {
             return fail(RTM_ERR_INVALID, "learned storage needs model sides that are multiples of 4");
         if (p->want_grad)
             return fail(RTM_ERR_INVALID, "learned storage serves imaging, not the gradient");
+    }
+    if (p->storage == RTM_STORE_DECIMATED) {
+        if (p->ckpt_every < 0 || p->ckpt_every > p->nt)
+            return fail(RTM_ERR_INVALID, "exact window %d outside [0, nt]", p->ckpt_every);
+        if (p->want_grad)
+            return fail(RTM_ERR_INVALID, "decimated storage serves imaging, not the gradient");
     }
     if (p->storage == RTM_STORE_CKPT && p->ckpt_every < 1)
         return fail(RTM_ERR_INVALID, "ckpt_every %d < 1", p->ckpt_every);
@@ -296,6 +311,9 @@ struct Ctx {
     bool snap_padded = false;   // imaging snapshots are padded fields (boundary storage)
 
     float* at(size_t off) const { return reinterpret_cast<float*>(ws + off); }
+    float* coarse_slot(size_t k) const {
+        return reinterpret_cast<float*>(ws + L.latent + k * L.latent_bytes);
+    }
     ae::bf16* latent_slot(size_t k) const {
         return reinterpret_cast<ae::bf16*>(ws + L.latent + k * L.latent_bytes);
     }
@@ -471,6 +489,8 @@ rtm_status run_forward(Ctx& C, const int32_t* rec, float* data, float* u_last) {
         // its squares for the encoder's scale (no separate pass over it)
         const bool code = p->storage == RTM_STORE_LEARNED && (n + 1) % ie == 0 &&
                           n + 1 > p->ckpt_every;
+        const bool decim = p->storage == RTM_STORE_DECIMATED && (n + 1) % ie == 0 &&
+                           n + 1 > p->ckpt_every;
         auto* scal = reinterpret_cast<ae::AeScalars*>(C.at(C.L.ae_scalars));
         if (code) {
             CU(cudaMemsetAsync(&scal->sumsq, 0, sizeof(double), C.s));
@@ -480,6 +500,10 @@ rtm_status run_forward(Ctx& C, const int32_t* rec, float* data, float* u_last) {
         if (p->storage == RTM_STORE_BOUNDARY && n + 1 <= p->nt - 2) {
             // the band of u^{n+1} (now in prev)
             CU(launch_band_copy(C.G, p->radius, prev, C.band_of(n + 1), 0, C.s));
+            count_launch();
+        }
+        if (decim) {  // u^{n+1} (now in prev): every other sample per axis
+            CU(launch_decimate(C.G, prev, C.coarse_slot((size_t)((n + 1) / ie - 1)), C.s));
             count_launch();
         }
         if (code) {
@@ -615,16 +639,19 @@ rtm_status run_backward(Ctx& C, const int32_t* rec, const float* rdata, float* s
         return RTM_OK;
     };
 
-    if (p->storage == RTM_STORE_LEARNED) {
+    if (p->storage == RTM_STORE_LEARNED || p->storage == RTM_STORE_DECIMATED) {
         const int W = p->ckpt_every;  // exact window: steps 1..W recomputed, not coded
         float* slab = C.snap_slot(0);
-        // columns outside the model stay finite (the decoder writes model columns)
+        // columns outside the model stay finite (the decoders write model columns)
         CU(cudaMemsetAsync(slab, 0, sizeof(float) * C.d.slab, C.s));
         for (int m = p->nt; m > W; m--) {
             if (m % ie == 0) {
                 const size_t k = (size_t)(m / ie - 1);
-                CU(ae_decode(C.ae, C.latent_slot(k), C.at(C.L.scales) + k, C.model_view(slab),
-                             nullptr, C.status(), C.s));
+                if (p->storage == RTM_STORE_DECIMATED)
+                    CU(launch_upsample(C.G, C.coarse_slot(k), slab, C.s));
+                else
+                    CU(ae_decode(C.ae, C.latent_slot(k), C.at(C.L.scales) + k,
+                                 C.model_view(slab), nullptr, C.status(), C.s));
                 count_launch(1);
             }
             CHECK(back_step(m, slab));

@@ -114,6 +114,11 @@ cudaError_t launch_grad_finalize(const Geometry& G, const float* acc, const floa
                                  double dx3, double dt2, float* grad_v2, cudaStream_t s);
 cudaError_t launch_misfit(const float* d, const float* obs, long long n, float* resid,
                           double* J, cudaStream_t s);
+// decimated storage (the non-learned 8x scheme): keep every other model
+// sample per axis of a padded field into coarse [(nz+1)/2][(ny+1)/2][(nx+1)/2];
+// reconstruct the model region of a snapshot slab by linear interpolation
+cudaError_t launch_decimate(const Geometry& G, const float* u, float* coarse, cudaStream_t s);
+cudaError_t launch_upsample(const Geometry& G, const float* coarse, float* slab, cudaStream_t s);
 // post-run check: any non-finite value among n floats sets *status to
 // RTM_ERR_NUMERIC (unless another error is already recorded)
 cudaError_t launch_finite_scan(const float* f, long long n, int* status, cudaStream_t s);

@@ -91,3 +91,72 @@ def reconstruction_error(params: torch.Tensor, snaps: torch.Tensor) -> float:
         num += float(((r - s) ** 2).sum())
         den += float((s * s).sum())
     return math.sqrt(num / max(den, 1e-300))
+
+
+def decimation_init(seed: int = 0) -> np.ndarray:
+    """Initial codec parameters (flat, float32) under which the network
+    computes the non-learned 8x scheme exactly, up to bfloat16 rounding:
+    keep every other sample on each axis, reconstruct by linear interpolation
+    along each axis. Training starts from that scheme instead of from noise.
+
+    * E1 channels 0 / 1: +x and -x of the sample at the even corner of each
+      2^3 patch (LeakyReLU(v) - LeakyReLU(-v) = 1.1 v recovers it).
+    * Latent channels 0..7: the eight kept samples of each 4^3 block, one per
+      parity (pz, py, px) of the half-resolution grid (E2's tap pz + 1).
+    * D1 channels c and 8 + c (c = child parity (az, ay, ax)): +/- the linear
+      interpolation of the kept samples at q and q + 1 on each axis for the
+      child 2q + a; a transposed-convolution tap k reads latent parity p as
+      sample q + d with (k, p) = (1, 0): d = 0, (1, 1): d = 1, (2, 1): d = 0,
+      (0, 0): d = 1, each weighted 1 / 0 (a = 0, d = 0 / 1) or 1/2 (a = 1).
+    * D2 maps the pair back to the child's sample.
+
+    Channels that carry the scheme read nothing else. The remaining channels
+    (E1 2..31, latent 8..15, D1 16..31) keep their seeded random weights;
+    D2 reads them with weight zero, so the initial output is the scheme's,
+    and training grows their share from there."""
+    P = rtm_inputs.ae_init_params(seed)
+    inv = 1.0 / 1.1
+    W1, W2, W3, W4 = P["W1"], P["W2"], P["W3"], P["W4"]
+    W1[0:2] = 0.0
+    W1[0, 0, 0, 0] = 1.0
+    W1[1, 0, 0, 0] = -1.0
+    W2[0:8] = 0.0
+    for pz in range(2):
+        for py in range(2):
+            for px in range(2):
+                o = 4 * pz + 2 * py + px
+                W2[o, pz + 1, py + 1, px + 1, 0] = inv
+                W2[o, pz + 1, py + 1, px + 1, 1] = -inv
+    # per axis: weight of (tap k, latent parity p) for child parity a
+    def w_axis(a, k, p):
+        d = {(1, 0): 0, (1, 1): 1, (2, 1): 0, (0, 0): 1}.get((k, p))
+        if d is None:
+            return 0.0
+        return 0.5 if a == 1 else (1.0 if d == 0 else 0.0)
+
+    W3[0:16] = 0.0
+    for az in range(2):
+        for ay in range(2):
+            for ax in range(2):
+                c = 4 * az + 2 * ay + ax
+                for kz in range(4):
+                    for ky in range(4):
+                        for kx in range(4):
+                            for pz in range(2):
+                                for py in range(2):
+                                    for px in range(2):
+                                        w = (w_axis(az, kz, pz) * w_axis(ay, ky, py) *
+                                             w_axis(ax, kx, px))
+                                        i = 4 * pz + 2 * py + px
+                                        W3[c, kz, ky, kx, i] = w
+                                        W3[8 + c, kz, ky, kx, i] = -w
+    W4[...] = 0.0
+    for az in range(2):
+        for ay in range(2):
+            for ax in range(2):
+                c = 4 * az + 2 * ay + ax
+                W4[az, ay, ax, c] = inv
+                W4[az, ay, ax, 8 + c] = -inv
+    for b in ("b1", "b2", "b3", "b4"):
+        P[b][...] = 0.0
+    return rtm_inputs.ae_flat(P).astype(np.float32)

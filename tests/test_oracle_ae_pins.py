@@ -138,6 +138,64 @@ def test_decimation_baseline_is_exact_on_affine_fields():
     np.testing.assert_allclose(up[s, s, s], f[s, s, s], rtol=0, atol=1e-6)
 
 
+@pytest.mark.parametrize("shape", [(9, 12, 7), (6, 5, 10), (1, 2, 3)])
+def test_decimation_baseline_matches_brute_force_on_non_cubic_grids(shape):
+    """The interpolation written as one weighted sum over the eight coarse
+    corners of each sample (per axis: an even sample j is the kept sample
+    j / 2; an odd one the mean of (j - 1) / 2 and (j + 1) / 2, or a copy of
+    (j - 1) / 2 past the last kept sample), sample by sample, against the
+    oracle's axis-by-axis sweeps, on odd and even sides."""
+    rng = np.random.default_rng(13)
+    s = rng.standard_normal(shape)
+    d = ae.decimate(s)
+    up = ae.trilinear_upsample(d, shape)
+    assert d.shape == tuple((n + 1) // 2 for n in shape)
+
+    def taps(j, nc):
+        if j % 2 == 0:
+            return [(j // 2, 1.0)]
+        if (j + 1) // 2 < nc:
+            return [((j - 1) // 2, 0.5), ((j + 1) // 2, 0.5)]
+        return [((j - 1) // 2, 1.0)]
+
+    ref = np.zeros(shape)
+    for z in range(shape[0]):
+        for y in range(shape[1]):
+            for x in range(shape[2]):
+                v = 0.0
+                for iz, wz in taps(z, d.shape[0]):
+                    for iy, wy in taps(y, d.shape[1]):
+                        for ix, wx in taps(x, d.shape[2]):
+                            v += wz * wy * wx * d[iz, iy, ix]
+                ref[z, y, x] = v
+    np.testing.assert_allclose(up, ref, rtol=0, atol=1e-12)
+    # the kept samples come back exactly (float32 storage)
+    np.testing.assert_array_equal(up[::2, ::2, ::2], s[::2, ::2, ::2].astype(np.float32))
+
+
+def test_decimation_initialised_network_computes_the_decimation_baseline():
+    """The codec's decimation-equivalent initial parameters make the oracle
+    network compute decimation + linear interpolation exactly (without
+    bfloat16 rounding) away from the upper faces, where the network's
+    transposed convolution sees zero padding instead of a copied sample;
+    with bfloat16 rounding within 1 %. This also checks the oracle's
+    transposed-convolution tap table independently of torch: a wrong (t, k)
+    pair breaks the interpolation."""
+    from paper_1603_03971_gb300 import learned
+
+    P = ae.unflatten(learned.decimation_init(3).astype(np.float64))
+    rng = np.random.default_rng(14)
+    for shape in [(16, 16, 16), (12, 8, 20)]:
+        s = rng.standard_normal(shape)
+        ref = ae.trilinear_upsample(ae.decimate(s), shape)
+        inner = tuple(slice(0, n - 1) for n in shape)
+        y = ae.forward(P, s, bf16=False)
+        np.testing.assert_allclose(y[inner], ref[inner], rtol=0, atol=1e-6)
+        yb = ae.forward(P, s, bf16=True)
+        err = np.linalg.norm(yb[inner] - ref[inner]) / np.linalg.norm(ref[inner])
+        assert err < 1e-2
+
+
 def test_encode_decode_compress_8x():
     rng = np.random.default_rng(10)
     s = rng.standard_normal((16, 16, 16))
