@@ -55,13 +55,17 @@ def training_snapshots(n_models: int = 64, size: int = 192, nb: int = 32, nt: in
 
 def train(data: torch.Tensor, steps: int = 1500, batch: int = 4, lr: float = 1e-3,
           lr_min: float = 5e-5, seed: int = 0, params: Optional[torch.Tensor] = None,
-          log_every: int = 0):
+          log_every: int = 0, init: str = "decimation"):
     """Adam on random mini-batches of ``data`` with a cosine learning-rate
-    decay from ``lr`` to ``lr_min``. Returns (params, losses)."""
+    decay from ``lr`` to ``lr_min``. Without ``params`` training starts from
+    ``init``: "decimation" (the network set to compute the non-learned 8x
+    scheme, ``decimation_init``) or "random" (seeded He-style weights).
+    Returns (params, losses)."""
     dev = data.device
     if params is None:
-        params = torch.from_numpy(
-            rtm_inputs.ae_flat(rtm_inputs.ae_init_params(seed)).astype(np.float32)).to(dev)
+        flat = (decimation_init(seed) if init == "decimation"
+                else rtm_inputs.ae_flat(rtm_inputs.ae_init_params(seed)))
+        params = torch.from_numpy(flat.astype(np.float32)).to(dev)
     m = torch.zeros_like(params)
     v = torch.zeros_like(params)
     ws = codec.alloc_workspace(tuple(data.shape[1:]), dev)
