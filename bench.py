@@ -54,11 +54,12 @@ def parse():
                     help="override the stencil radius (profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--ref-steps", type=int, default=2,
-                    help="oracle time steps per bench step of the reference arm")
+    ap.add_argument("--ref-steps", type=int, default=20,
+                    help="oracle time steps per bench step of the reference arm (the same "
+                         "sample as the CPU baseline of our arm)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-compression leg (384^3, 3000 steps)")
-    ap.add_argument("--learned-train-steps", type=int, default=20000)
+    ap.add_argument("--learned-train-steps", type=int, default=8000)
     ap.add_argument("--learned-models", type=int, default=64)
     ap.add_argument("--learned-window", type=int, default=200,
                     help="exact window: the first steps whose snapshots are recomputed from the "
@@ -71,8 +72,12 @@ def parse():
                     help="skip the velocity-gradient leg (gradient_256 workload)")
     ap.add_argument("--no-boundary", action="store_true",
                     help="skip the boundary-storage shot (reverse time stepping)")
-    ap.add_argument("--batch", action="store_true",
-                    help="also run the batched-shots leg (32 apertures, radius 8)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched-shots leg (32 apertures, radius 8)")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the two-layer 64^3 full-RTM leg (per-shot time, CUDA graph)")
+    ap.add_argument("--no-r8", action="store_true",
+                    help="skip the radius-8 leg (smooth 512^3 model, 200 steps)")
     ap.add_argument("--batch-nt", type=int, default=1500)
     ap.add_argument("--batch-shots", default="all",
                     help="comma-separated aperture indices of the batched workload (default all 32)")
@@ -258,22 +263,47 @@ def profiled_traffic(radius: int, tile_rows: int, padded_shape):
 # CPU oracle timing (baseline and reference arm)
 # ----------------------------------------------------------------------------
 
-def oracle_sample(w, vel_np, steps: int):
-    """Time ``steps`` forward time steps of the FP64 oracle on the full padded
-    grid of the workload; returns (seconds, updates, threads)."""
-    import numpy as np
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the
+    machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
 
+    return platform.machine()
+
+
+def oracle_sample(w, vel_np, steps: int, lead: int = 3):
+    """Time ``steps`` forward time steps of the FP64 oracle on the full padded
+    grid of the workload, without its allocation: the oracle allocates and
+    first touches its fields inside a forward call, within its first few
+    steps, so the sample is the difference of a (lead + steps)-step and a
+    lead-step run on the same prepared grid. Returns (seconds, updates,
+    threads)."""
     import oracle
 
     rec = w.receivers()[:1]
-    p = oracle.Problem(vel_np, w.nb, w.radius, w.dx, w.dt, steps, w.f0, w.t0, w.src, rec)
+    p = oracle.Problem(vel_np, w.nb, w.radius, w.dx, w.dt, lead + steps, w.f0, w.t0, w.src, rec)
     t = time.perf_counter()
-    p.forward()
-    el = time.perf_counter() - t
-    NZ, NY, NX = w.padded_shape
+    p.grid.forward(p.w[:lead], p.src, p.rec)
+    t_short = time.perf_counter() - t
+    t = time.perf_counter()
+    p.grid.forward(p.w, p.src, p.rec)
+    t_long = time.perf_counter() - t
     del p
-    np.zeros(1)
-    return el, steps * NX * NY * NZ, oracle.num_threads()
+    NZ, NY, NX = w.padded_shape
+    return max(t_long - t_short, 1e-9), steps * NX * NY * NZ, oracle.num_threads()
 
 
 def run_reference(args):
@@ -292,8 +322,8 @@ def run_reference(args):
         vel = v.double().cpu().numpy() if hasattr(v, "cpu") else v
     vel = np.asarray(vel, dtype=np.float64)
     NZ, NY, NX = w.padded_shape
-    for _ in range(args.warmup):
-        oracle_sample(w, vel, args.ref_steps)
+    for _ in range(args.warmup):  # warm-up samples of two steps
+        oracle_sample(w, vel, min(args.ref_steps, 2))
     total_s, total_u, threads = 0.0, 0, 1
     for _ in range(args.steps):
         s, u, threads = oracle_sample(w, vel, args.ref_steps)
@@ -301,7 +331,8 @@ def run_reference(args):
         total_u += u
     value = total_u / total_s / 1e9
     sample = ("%d forward time steps of the FP64 oracle on the %dx%dx%d padded grid per bench "
-              "step" % (args.ref_steps, NX, NY, NZ))
+              "step, allocation and first touch excluded (a %d-step run minus a 3-step run)"
+              % (args.ref_steps, NX, NY, NZ, args.ref_steps + 3))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -309,7 +340,7 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_of(w),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -336,7 +367,7 @@ def learned_leg(args, dev):
     data = learned.training_snapshots(n_models=args.learned_models, size=192, nt=1200, every=40,
                                       first=40, device=dev)
     P, losses = learned.train(data, steps=args.learned_train_steps, batch=4, lr=1e-3,
-                              lr_min=5e-5, log_every=0)
+                              lr_min=5e-5, log_every=0, init="decimation")
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     n_snap = int(data.shape[0])
@@ -373,18 +404,44 @@ def learned_leg(args, dev):
     t_ckpt = e0.elapsed_time(e1) / 1e3
     ws_ckpt_gb = ws.numel() / 1e9
     del ws
-    pl = rtm.params_for(w, storage="learned", ckpt_every=args.learned_window)
-    wl = rtm.alloc_workspace(pl, dev)
-    img_l = torch.zeros_like(img_c)
-    rtm.shot_learned(pl, c, rec, dobs, P, wl, img_l)  # warm-up
-    img_l.zero_()
-    torch.cuda.synchronize()
-    e0.record()
-    rtm.shot_learned(pl, c, rec, dobs, P, wl, img_l)
-    e1.record()
-    torch.cuda.synchronize()
-    t_learned = e0.elapsed_time(e1) / 1e3
-    rtm.check(wl)
+
+    def run(storage, window):
+        """One timed shot (after a warm-up) with learned or decimated storage
+        and the given exact window; returns (seconds, image rel-L2 against the
+        checkpoint image, the same below the top 16 model layers, workspace GB)."""
+        q = rtm.params_for(w, storage=storage, ckpt_every=window)
+        wq = rtm.alloc_workspace(q, dev)
+        img = torch.zeros_like(img_c)
+
+        def once():
+            if storage == "learned":
+                rtm.shot_learned(q, c, rec, dobs, P, wq, img)
+            else:
+                rtm.shot(q, c, rec, dobs, wq, img)
+        once()
+        img.zero_()
+        torch.cuda.synchronize()
+        e0.record()
+        once()
+        e1.record()
+        torch.cuda.synchronize()
+        rtm.check(wq)
+        t = e0.elapsed_time(e1) / 1e3
+        e = float((img - img_c).norm() / img_c.norm())
+        ed = float((img[16:] - img_c[16:]).norm() / img_c[16:].norm())
+        gb = wq.numel() / 1e9
+        del wq, img
+        return t, e, ed, gb
+
+    W = args.learned_window
+    t_learned, err, err_deep, ws_l_gb = run("learned", W)
+    t_dec, err_dec, err_dec_deep, ws_d_gb = run("decimated", W)
+    no_window = None
+    if W > 0:
+        tl0, el0, _, _ = run("learned", 0)
+        td0, ed0, _, _ = run("decimated", 0)
+        no_window = {"shot_s_learned": tl0, "image_rel_l2_learned": el0,
+                     "shot_s_decimated": td0, "image_rel_l2_decimated": ed0}
     from paper_1603_03971_gb300 import codec
 
     enc_ms, dec_ms = codec._time_codec(w.nx, reps=10)
@@ -407,25 +464,30 @@ def learned_leg(args, dev):
     }
     codec_tc["encode_frac"] = codec_tc["encode_tflops"] / bf16
     codec_tc["decode_frac"] = codec_tc["decode_tflops"] / bf16
-    err = float((img_l - img_c).norm() / img_c.norm())
-    err_deep = float((img_l[16:] - img_c[16:]).norm() / img_c[16:].norm())
     NZ, NY, NX = w.padded_shape
     return {
         "workload": "learned_384: 384^3 model (448^3 padded), r=4, 3000 steps, smooth random "
                     "velocity, imaging every 4 steps (750 snapshots); observed data: scattered "
                     "field of three thin beds (+-8 %) at depths 96/192/288",
         "shot_s_checkpoint": t_ckpt, "checkpoint_every": 50,
-        "workspace_gb_checkpoint": ws_ckpt_gb, "workspace_gb_learned": wl.numel() / 1e9,
-        "exact_window_steps": args.learned_window,
-        "coded_snapshots": (w.nt - args.learned_window) // w.image_every,
-        "window_snapshots": args.learned_window // w.image_every,
+        "workspace_gb_checkpoint": ws_ckpt_gb, "workspace_gb_learned": ws_l_gb,
+        "exact_window_steps": W,
+        "coded_snapshots": (w.nt - W) // w.image_every,
+        "window_snapshots": W // w.image_every,
         "shot_s_learned": t_learned, "speedup_vs_checkpoint": t_ckpt / t_learned,
         "image_rel_l2_vs_checkpoint": err, "target_rel_l2": 1e-2,
         "image_rel_l2_below_z16": err_deep,
+        # the non-learned 8x scheme at the same bytes and window: every other
+        # sample per axis in float32, linear interpolation
+        "decimated": {"shot_s": t_dec, "speedup_vs_checkpoint": t_ckpt / t_dec,
+                      "image_rel_l2_vs_checkpoint": err_dec,
+                      "image_rel_l2_below_z16": err_dec_deep, "workspace_gb": ws_d_gb},
+        "learned_over_decimated_error_ratio": err / err_dec if err_dec > 0 else None,
+        "no_window": no_window,
         "codec_ms_per_snapshot": {"encode": enc_ms, "decode": dec_ms},
         "codec_tensor": codec_tc,
         "compression": "8x (float32 snapshot -> 16 bfloat16 channels per 4^3 voxels)",
-        "train": {"models": args.learned_models, "snapshots": n_snap,
+        "train": {"models": args.learned_models, "snapshots": n_snap, "init": "decimation",
                   "steps": args.learned_train_steps, "batch": 4, "seconds": train_s,
                   "final_loss": losses[-1][1]},
         "updates_per_shot_learned": 2 * w.nt * NX * NY * NZ,
@@ -611,6 +673,105 @@ def grad_leg(dev, autotune=True):
            "tuning": tuned}
     del ws
     return res
+
+
+def small_leg(dev):
+    """The two-layer 64^3 workload (104^3 padded, 300 steps, store every
+    snapshot): a full RTM shot (forward with snapshot writes, receiver
+    propagation with imaging) per step, launched directly and replayed from
+    one CUDA graph of the same call (the workload is launch-bound: 1202
+    launches of about 10 us of work each)."""
+    import torch
+
+    import paper_1603_03971_gb300 as rtm
+    import rtm_inputs
+
+    w = rtm_inputs.WORKLOADS["two_layer_64"]
+    tuned = tune_shape(w.radius, w.padded_shape)
+    p = rtm.params_for(w)
+    ws = rtm.alloc_workspace(p, dev)
+    c = rtm.model_prep(p, torch.from_numpy(w.velocity_model()).float().to(dev).contiguous(), ws)
+    rec = torch.from_numpy(w.receivers()).to(dev)
+    dobs = torch.empty((w.nt, p.nrec), dtype=torch.float32, device=dev)
+    rtm.forward(p, c, rec, ws, data=dobs)
+    img = torch.zeros((w.nz, w.ny, w.nx), dtype=torch.float32, device=dev)
+    reps = 20
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for _ in range(3):
+        rtm.shot(p, c, rec, dobs, ws, img)
+    rtm.check(ws)
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(reps):
+        rtm.shot(p, c, rec, dobs, ws, img)
+    ev[1].record()
+    torch.cuda.synchronize()
+    t_direct = ev[0].elapsed_time(ev[1]) / 1e3 / reps
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        rtm.shot(p, c, rec, dobs, ws, img)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(reps):
+        g.replay()
+    ev[1].record()
+    torch.cuda.synchronize()
+    t_graph = ev[0].elapsed_time(ev[1]) / 1e3 / reps
+    rtm.check(ws)
+    NZ, NY, NX = w.padded_shape
+    updates = 2 * w.nt * NX * NY * NZ
+    del g, ws
+    return {"workload": "two_layer_64: 64^3 two-layer model (104^3 padded), r=4, 300 steps, "
+                        "15 Hz Ricker, 64x64 receivers, every snapshot stored",
+            "shot_s": t_direct, "shot_s_graph": t_graph,
+            "gpoint_updates_per_s": updates / t_direct / 1e9,
+            "gpoint_updates_per_s_graph": updates / t_graph / 1e9,
+            "updates_per_shot": updates, "tuning": tuned}
+
+
+def r8_leg(dev, hbm):
+    """The single-shot workload with the radius-8 (16th-order) stencil: 512^3
+    smooth random model (576^3 padded), 200 steps, checkpoints every 50, one
+    full checkpointed RTM shot; per-mode bandwidth from the live statistics
+    against the measured HBM copy rate."""
+    import torch
+
+    import paper_1603_03971_gb300 as rtm
+    import rtm_inputs
+
+    w = rtm_inputs.WORKLOADS["smooth_512"].scaled(radius=8, nt=200)
+    tuned = tune_shape(w.radius, w.padded_shape)
+    p = rtm.params_for(w)
+    ws = rtm.alloc_workspace(p, dev)
+    c = rtm.model_prep(p, w.velocity_model(device=dev).contiguous(), ws)
+    rec = torch.from_numpy(w.receivers()).to(dev)
+    dobs = torch.empty((w.nt, p.nrec), dtype=torch.float32, device=dev)
+    rtm.forward(p, c, rec, ws, data=dobs)
+    img = torch.zeros((w.nz, w.ny, w.nx), dtype=torch.float32, device=dev)
+    rtm.shot(p, c, rec, dobs, ws, img)  # warm-up
+    torch.cuda.synchronize()
+    rtm.reset_stats()
+    rtm.set_timing(True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    rtm.shot(p, c, rec, dobs, ws, img)
+    ev[1].record()
+    torch.cuda.synchronize()
+    rtm.set_timing(False)
+    st = rtm.stats()
+    rtm.check(ws)
+    t = ev[0].elapsed_time(ev[1]) / 1e3
+    NZ, NY, NX = w.padded_shape
+    modes = {k: {"ms_per_launch": v["ms"] / v["launches"], "gbs": v["bytes"] / v["ms"] / 1e6,
+                 "frac": v["bytes"] / v["ms"] / 1e6 / hbm}
+             for k, v in st["stencil"].items() if v["launches"] and v["ms"] > 0}
+    del ws
+    return {"workload": "smooth_512 at radius 8: 512^3 model (576^3 padded), r=8 (16th order), "
+                        "200 steps, checkpoint every 50",
+            "shot_s": t, "gpoint_updates_per_s": 3 * w.nt * NX * NY * NZ / t / 1e9,
+            "stencil_modes": modes, "tuning": tuned}
 
 
 def batch_leg(args, dev):
@@ -822,20 +983,32 @@ def run_ours(args):
         learned = learned_leg(args, dev)
         ws = None
     batch_res = None
-    if rank == 0 and args.batch:
+    if rank == 0 and not args.no_batch:
         ws = None
         torch.cuda.empty_cache()
         batch_res = batch_leg(args, dev)
+    small_res = None
+    if rank == 0 and not args.no_small:
+        ws = None
+        torch.cuda.empty_cache()
+        small_res = small_leg(dev)
+    r8_res = None
+    if rank == 0 and not args.no_r8:
+        ws = None
+        torch.cuda.empty_cache()
+        r8_res = r8_leg(dev, hbm)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ws = None
         torch.cuda.empty_cache()
-        steps = 20 if NX * NY * NZ > 50_000_000 else 50
+        steps = 20
         s, u, threads = oracle_sample(w, vel64, steps)
         cpu = {"value": u / s / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "%d forward time steps of the FP64 oracle on the %dx%dx%d padded "
-                         "grid (%.1f s)" % (steps, NX, NY, NZ, s)}
+                         "grid (%.1f s), allocation and first touch excluded (a %d-step run "
+                         "minus a 3-step run)" % (steps, NX, NY, NZ, s, steps + 3),
+               "cpu": cpu_model()}
 
     if rank == 0:
         line = {
@@ -846,6 +1019,7 @@ def run_ours(args):
             "config": cfg, "shot_s": t_max / args.steps, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": st["launches"],
             "clocks": clocks, "impl": "ours", "learned": learned, "batch": batch_res,
+            "two_layer_64": small_res, "radius8": r8_res,
             "imaging": imaging_res, "revolve": revolve_res, "boundary": boundary_res,
             "gradient": grad_res,
             # the paper's own reported improvements (relative speedups of a CPU

@@ -463,6 +463,49 @@ rtm_status rtm_batch(const rtm_params *p, int32_t nshots, const rtm_aperture *h_
 rtm_status rtm_forward_noalloc(const rtm_params *p, const float *d_c, const int32_t *d_rec,
                                float *d_data, float *d_u_last, rtm_stream stream);
 
+/* ---- X-Y domain decomposition of one shot ----------------------------------
+ * The paper's distributed time step (Sec. II): the padded grid is split in x
+ * and y into px x py subdomains, each holding its owned block plus an r-wide
+ * halo on its four x-y faces. Every step applies the stencil to the bands of
+ * tiles along the faces that have a neighbour first, packs the r-wide strips
+ * the neighbours need, exchanges them on a communication stream (the
+ * dedicated communication thread of Sec. III) while the interior is
+ * computed, and unpacks them into the neighbours' halos before the next
+ * step. All subdomains of a call live on the calling GPU; a strip's exchange
+ * is a device copy between pack and unpack buffers.
+ *
+ * Partition: x boundaries at multiples of 4 cells (as even as possible),
+ * y boundaries as even as possible; every part at least r (and 4 in x) wide.
+ * rtm_decomp_plan (host only, no device access) writes 8 int32 per subdomain
+ * (index j * px + i) into h_out: owned padded x0, x1, y0, y1 and the
+ * neighbour across the W (x-), E (x+), S (y-), N (y+) face, -1 at the grid's
+ * outer faces; returns px * py (h_out untouched if more than max_sub), or -1
+ * if p or the decomposition is invalid (rtm_last_error says why). */
+int32_t rtm_decomp_plan(const rtm_params *p, int32_t px, int32_t py, int32_t *h_out,
+                        int32_t max_sub);
+
+/* Workspace bytes of rtm_forward_decomposed (0 if invalid): the subdomains'
+ * local fields, coefficients and profiles, pack and unpack buffers, strip
+ * descriptors and per-subdomain receiver lists and traces. */
+size_t rtm_decomp_workspace_size(const rtm_params *p, int32_t px, int32_t py);
+
+/* Forward modelling (source injection, propagation, receiver gather) on the
+ * decomposition: d_c [NZ][NY][NX] as for rtm_forward (copied into the
+ * subdomains' local arrays at the start), d_rec [nrec][3] device array (read
+ * back to the host once to assign receivers to subdomains: the call
+ * synchronises the stream before its first launch), d_data [nt][nrec] or
+ * NULL, d_u_last [2][NZ][NY][NX] or NULL. storage must be RTM_STORE_ALL or
+ * RTM_STORE_CKPT (nothing is stored; no snapshots or checkpoints for a
+ * backward call) and want_grad 0. Needs the TMA stencil (tuning variant 2 or
+ * 3 gives the tile; otherwise 8-row tiles). The results equal rtm_forward's
+ * with the same tile bit for bit. A receiver outside the padded grid gets a
+ * zero trace and sets RTM_ERR_INVALID in the status word (rtm_check on
+ * d_ws); the post-run scan of u^nt applies. The call creates and destroys
+ * one stream and two events of its own. */
+rtm_status rtm_forward_decomposed(const rtm_params *p, int32_t px, int32_t py, const float *d_c,
+                                  const int32_t *d_rec, float *d_data, void *d_ws,
+                                  size_t ws_bytes, float *d_u_last, rtm_stream stream);
+
 /* Stencil tuning: z extent of the slab one thread block marches through
  * (0 = automatic) and the plane-load path and tile (0 = automatic: TMA
  * where the driver provides tensor maps; 1 = 16-byte vector loads through

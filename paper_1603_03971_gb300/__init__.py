@@ -25,7 +25,8 @@ __all__ = [
     "host_workspace_size", "alloc_workspace", "model_prep", "forward", "backward_image",
     "shot", "grad", "misfit", "check", "shot_host", "forward_learned",
     "backward_image_learned", "shot_learned", "snapshot", "set_tuning", "set_timing", "stats",
-    "reset_stats", "RtmMisfit", "version",
+    "reset_stats", "RtmMisfit", "version", "decomp_plan", "decomp_workspace_size",
+    "forward_decomposed",
 ]
 
 
@@ -229,6 +230,41 @@ def misfit(d, obs, resid=None, J=None, stream=None):
     call("rtm_misfit", _dev(d, name="d"), _dev(obs, name="obs"), ctypes.c_int64(d.numel()),
          _dev(resid, name="resid"), _dev(J, torch.float64, "J"), _stream(stream))
     return J, resid
+
+
+def decomp_plan(p: RtmParams, px: int, py: int):
+    """The X-Y decomposition of the padded grid into px x py subdomains (host
+    only): one row per subdomain (index j * px + i) of owned padded ranges
+    x0, x1, y0, y1 and the neighbours across the W, E, S, N faces (-1 at the
+    grid's outer faces)."""
+    import numpy as np
+
+    n = px * py
+    out = np.zeros((max(n, 1), 8), dtype=np.int32)
+    got = lib().rtm_decomp_plan(ctypes.byref(p), int(px), int(py),
+                                out.ctypes.data_as(ctypes.c_void_p), n)
+    if got < 0:
+        raise RtmError(1, "rtm_decomp_plan", (lib().rtm_last_error() or b"").decode())
+    return out[:n]
+
+
+def decomp_workspace_size(p: RtmParams, px: int, py: int) -> int:
+    n = lib().rtm_decomp_workspace_size(ctypes.byref(p), int(px), int(py))
+    if n == 0:
+        raise RtmError(1, "rtm_decomp_workspace_size", (lib().rtm_last_error() or b"").decode())
+    return int(n)
+
+
+def forward_decomposed(p: RtmParams, px: int, py: int, c, rec, ws, data=None, u_last=None,
+                       stream=None):
+    """Forward modelling on a px x py X-Y decomposition with the halo exchange
+    overlapped with the interior stencil (one GPU); same outputs as
+    ``forward``."""
+    w, wb = _ws(ws)
+    call("rtm_forward_decomposed", ctypes.byref(p), int(px), int(py), _dev(c, name="c"),
+         _dev(rec, torch.int32, "rec"), _dev(data, name="data"), w, wb,
+         _dev(u_last, name="u_last"), _stream(stream))
+    return data, u_last
 
 
 def check(ws, stream=None):

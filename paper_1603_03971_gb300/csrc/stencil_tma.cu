@@ -271,7 +271,12 @@ __global__ void __launch_bounds__(16 * BY, (tma_min_blocks<R, MODE, BY>()))
     const int x = x0 + V * tx, y = y0 + ty;
     const int zb = A.zorg + blockIdx.z * A.zchunk;
     const int ze = min(A.zend, zb + A.zchunk);
-    const bool own = x < A.NX && y < A.NY;
+    // cells this thread updates: inside the array and the launch region (a
+    // vector straddling the region's x end is computed whole; a launch over
+    // one subdomain of a decomposed grid leaves its halo columns and rows
+    // untouched: their end is a multiple of V)
+    const int xend_v = (A.xend + V - 1) / V * V;
+    const bool own = x < A.NX && y < A.NY && x < xend_v && y < A.yend;
     const size_t plane = (size_t)A.NX * (size_t)A.NY;
     const size_t col = (size_t)y * A.NX + x;
     const bool xm = (x + V - 1 >= A.nb) && (x < A.nb + A.nx);

@@ -10,7 +10,7 @@ from __future__ import annotations
 
 import math
 import time
-from typing import Optional
+from typing import Optional, Sequence
 
 import numpy as np
 import torch
@@ -24,22 +24,25 @@ from . import (alloc_workspace, forward, make_params, model_prep, snapshot)
 def training_snapshots(n_models: int = 64, size: int = 192, nb: int = 32, nt: int = 1200,
                        every: int = 100, first: int = 200, f0: float = 20.0, seed0: int = 1000,
                        dx: float = 10.0, vmin: float = 1500.0, vmax: float = 4500.0,
-                       device="cuda") -> torch.Tensor:
+                       device="cuda", early: Sequence[int] = ()) -> torch.Tensor:
     """Snapshots [S][size][size][size] (float32, on the device) of forward
     modelling on ``n_models`` seeded smooth random models (sigma 8 cells,
     [vmin, vmax]); one surface source per model at a seeded position; the
-    snapshots at the multiples of ``every`` from ``first`` to ``nt``."""
+    snapshots at the steps in ``early`` and at the multiples of ``every``
+    from ``first`` to ``nt``."""
     dt = rtm_inputs.courant_dt(dx, vmax)
     rng = np.random.Generator(np.random.PCG64(seed0))
-    steps = list(range(every * max(1, -(-first // every)), nt + 1, every))
+    steps = sorted(set(int(m) for m in early if 1 <= m <= nt) |
+                   set(range(every * max(1, -(-first // every)), nt + 1, every)))
     out = torch.empty((n_models * len(steps), size, size, size), dtype=torch.float32,
                       device=device)
     k = 0
     for i in range(n_models):
         src = (int(rng.integers(size // 4, 3 * size // 4)),
                int(rng.integers(size // 4, 3 * size // 4)), 4)
+        step_every = math.gcd(*steps) if steps else every
         p = make_params(size, size, size, nb, 4, nt, dx, dt, f0, 1.0 / f0, src, 1,
-                        storage="all", image_every=every)
+                        storage="all", image_every=step_every)
         ws = alloc_workspace(p, device)
         v = rtm_inputs.smooth_random_velocity(size, size, size, 8.0, vmin, vmax,
                                               seed=seed0 + 1 + i, device=device)

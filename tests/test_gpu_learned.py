@@ -5,13 +5,13 @@ source snapshots.
    end in FP64 on the CPU (propagation, codec with bfloat16 rounding at the
    GPU's storage points, receiver propagation and imaging). The image is
    linear in the decoded snapshots, so the codec tolerance (2e-3) bounds it.
-2. Gain: a codec trained (by the library's own kernels) on snapshots the
-   propagator generated from other random models reconstructs and images
-   far closer to the exact snapshots and image than the untrained network.
-   All images here are the GPU's own (store-all vs learned storage); the
-   non-learned 8x baseline (decimation by 2 per axis + linear
-   interpolation) is printed beside them at the snapshot level; at this
-   training budget it is not beaten, and the test does not claim it.
+2. Gain: a codec trained (by the library's own kernels, starting from the
+   parameters under which the network computes the non-learned 8x scheme)
+   on snapshots the propagator generated from other random models
+   reconstructs and images closer to the exact snapshots and image than
+   that scheme at the same bytes (decimated storage) and than the untrained
+   network. All images here are the GPU's own (store-all vs learned vs
+   decimated storage).
 """
 import numpy as np
 import pytest
@@ -93,15 +93,22 @@ def test_exact_window_over_the_whole_run_is_the_store_all_image():
     np.testing.assert_array_equal(img, ref)
 
 
-def test_trained_codec_beats_the_untrained_network():
-    """The codec's gain from training: trained on snapshots of 16 other random
-    models, it reconstructs held-out snapshots far better than the same
-    network untrained, and its RTM image (learned storage) is
-    correspondingly closer to the store-all image."""
+def test_trained_codec_beats_the_decimation_scheme_and_the_untrained_network():
+    """What the trained network gains over the method without it. The codec
+    starts from the decimation-equivalent parameters (the network computing
+    the non-learned 8x scheme) and is trained by the library's own kernels on
+    snapshots of 16 other random models. On held-out snapshots and in the RTM
+    image it beats
+
+    * the non-learned 8x scheme at the same bytes (decimated storage: every
+      other sample per axis in float32, linear interpolation), and
+    * the same network with random weights (untrained),
+
+    with the images of all three storage modes compared against the
+    store-all image of the same shot."""
     import torch
 
     from helpers import DeviceShot
-    from oracle import ae as oae
     import paper_1603_03971_gb300 as rtm
     from paper_1603_03971_gb300 import codec, learned
 
@@ -109,8 +116,8 @@ def test_trained_codec_beats_the_untrained_network():
     data = learned.training_snapshots(n_models=16, size=n, nb=16, nt=640, every=20, first=40,
                                       f0=20.0, seed0=500)
     P, losses = learned.train(data, steps=800, batch=4, lr=1e-3, lr_min=5e-5, seed=1,
-                              log_every=100)
-    assert losses[-1][1] < 0.5 * losses[0][1]
+                              log_every=100, init="decimation")
+    print("training losses:", [(s, round(v, 5)) for s, v, _ in losses])
     ie = 8
     case = Case(nx=n, ny=n, nz=n, nb=16, r=4, nt=480, image_every=ie, f0=20.0, t0=0.05,
                 vmax=4500.0, src=(48, 40, 4), rec_stride=3, seed=77, sigma=8.0)
@@ -120,6 +127,7 @@ def test_trained_codec_beats_the_untrained_network():
     d_obs = case.d_obs(g.nrec)
     img_exact = g.backward_image(d_obs)[0].cpu().numpy().astype(np.float64)
     P0 = torch.from_numpy(rtm_inputs.ae_flat(rtm_inputs.ae_init_params(1)).astype(np.float32)).cuda()
+    PD = torch.from_numpy(learned.decimation_init(1)).cuda()
     ws = codec.alloc_workspace((n, n, n))
 
     def snap_err(params):
@@ -131,20 +139,31 @@ def test_trained_codec_beats_the_untrained_network():
             den += float((s.double() ** 2).sum())
         return (num / den) ** 0.5
 
-    e_tr, e_un = snap_err(P), snap_err(P0)
+    e_tr, e_un, e_init = snap_err(P), snap_err(P0), snap_err(PD)
+    # decimated storage on the GPU, its image and (through its snapshots,
+    # rebuilt by the oracle's scheme) its snapshot error
+    from oracle import ae as oae
+
     num = den = 0.0
-    for s in exact.values():  # printed reference only
+    for s in exact.values():
         sn = s.cpu().numpy().astype(np.float64)
         num += float(np.sum((oae.trilinear_upsample(oae.decimate(sn), n) - sn) ** 2))
         den += float(np.sum(sn ** 2))
     e_de = (num / den) ** 0.5
-    img = {"trained": _learned_image(case, g, P, d_obs), "untrained": _learned_image(case, g, P0, d_obs)}
-    ie_tr, ie_un = (rel_l2(img[k], img_exact) for k in ("trained", "untrained"))
-    deep = slice(8, None)
-    dd = {k: rel_l2(img[k][deep], img_exact[deep]) for k in img}
-    print("snapshot rel-L2: trained %.3e untrained %.3e decimation %.3e" % (e_tr, e_un, e_de))
-    print("image rel-L2: trained %.3e untrained %.3e" % (ie_tr, ie_un))
-    print("image rel-L2 below z=8: %s" % {k: round(v, 4) for k, v in dd.items()})
+    pd = case.params()
+    pd.storage = rtm.RTM_STORE_DECIMATED
+    wd = rtm.alloc_workspace(pd)
+    img_d = torch.zeros((n, n, n), device="cuda")
+    rtm.shot(pd, g.c, g.rec, torch.from_numpy(d_obs.astype(np.float32)).cuda(), wd, img_d)
+    rtm.check(wd)
+    img = {"trained": _learned_image(case, g, P, d_obs),
+           "untrained": _learned_image(case, g, P0, d_obs),
+           "decimated": img_d.cpu().numpy().astype(np.float64)}
+    ie_ = {k: rel_l2(v, img_exact) for k, v in img.items()}
+    print("snapshot rel-L2: trained %.3e decimation %.3e (network at its initial "
+          "parameters %.3e) untrained %.3e" % (e_tr, e_de, e_init, e_un))
+    print("image rel-L2: %s" % {k: round(v, 5) for k, v in ie_.items()})
+    assert e_tr < 0.9 * e_de
+    assert ie_["trained"] < 0.9 * ie_["decimated"]
     assert e_tr < 0.25 * e_un
-    assert ie_tr < 0.6 * ie_un
-    assert dd["trained"] < 0.25 * dd["untrained"]
+    assert ie_["trained"] < 0.25 * ie_["untrained"]
