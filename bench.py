@@ -619,7 +619,8 @@ def tune_shape(radius, padded_shape):
     from paper_1603_03971_gb300 import autotune
 
     choice = autotune.apply(radius, tuple(int(v) for v in padded_shape))
-    return {"zchunk": choice["zchunk"], "variant": choice["variant"]} if choice else None
+    return ({"zchunk": choice["zchunk"], "variant": choice["variant"],
+             "zchunk_modes": choice.get("zchunk_modes", {})} if choice else None)
 
 
 def grad_leg(dev, autotune=True):

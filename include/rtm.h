@@ -521,6 +521,15 @@ rtm_status rtm_forward_decomposed(const rtm_params *p, int32_t px, int32_t py, c
  * height from its own argument. */
 rtm_status rtm_set_tuning(int32_t radius, int32_t zchunk, int32_t variant);
 
+/* Slab height of one stencil mode at a radius (0 = the radius's general
+ * slab height), set after rtm_set_tuning (which clears these): mode 0
+ * forward step (and the learned forward step that sums squares), 1 forward +
+ * snapshot, 2 backward + imaging, 3 forward + L u, 4 backward + gradient,
+ * 6 reverse step of boundary storage. The modes move different bytes per
+ * point, so their best slab heights differ; the autotuner sets them from
+ * the per-mode timings of its trials. Applies to the single-shot calls. */
+rtm_status rtm_set_tuning_mode(int32_t radius, int32_t mode, int32_t zchunk);
+
 /* Enable (1) or disable (0) per-launch CUDA-event timing of the stencil
  * kernels. While enabled, each API call synchronises its stream on return. */
 rtm_status rtm_set_timing(int32_t enable);

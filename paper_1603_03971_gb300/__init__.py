@@ -303,6 +303,15 @@ def set_tuning(radius: int, zchunk: int = 0, variant: int = 0):
     call("rtm_set_tuning", radius, zchunk, variant)
 
 
+MODE_SLOTS = {"fwd": 0, "fwd_snap": 1, "bwd_image": 2, "fwd_lu": 3, "bwd_grad": 4, "rev": 6}
+
+
+def set_tuning_mode(radius: int, mode: str, zchunk: int):
+    """Slab height of one stencil mode (a key of ``MODE_SLOTS``); cleared by
+    ``set_tuning``."""
+    call("rtm_set_tuning_mode", radius, MODE_SLOTS[mode], zchunk)
+
+
 def set_timing(enable: bool):
     call("rtm_set_timing", 1 if enable else 0)
 

@@ -81,6 +81,7 @@ SIGNATURES = {
     "rtm_check": (ctypes.c_int, [_vp, _sz, _vp]),
     "rtm_forward_noalloc": (ctypes.c_int, [_P, _vp, _vp, _vp, _vp, _vp]),
     "rtm_set_tuning": (ctypes.c_int, [_i32, _i32, _i32]),
+    "rtm_set_tuning_mode": (ctypes.c_int, [_i32, _i32, _i32]),
     "rtm_decomp_plan": (ctypes.c_int32, [_P, _i32, _i32, _vp, _i32]),
     "rtm_decomp_workspace_size": (_sz, [_P, _i32, _i32]),
     "rtm_forward_decomposed": (ctypes.c_int, [_P, _i32, _i32, _vp, _vp, _vp, _vp, _sz, _vp,

@@ -2,7 +2,8 @@
 
 For a stencil radius and a padded grid shape it times a short checkpointed
 shot of ``rtm_shot`` (forward, recompute with snapshot writes, backward with
-imaging: every kernel mode of a shot, whose best slab heights differ) or a
+imaging: every kernel mode of a shot, whose best slab heights differ; the
+per-launch timing of each mode picks a slab height per mode) or a
 short ``rtm_batch`` (persistent multi-shot kernel) for each candidate z-slab
 height (and plane-load variant where there is more than one), with CUDA
 events after a warm-up, picks the fastest and caches the choice in a JSON
@@ -60,10 +61,11 @@ def candidates(NZ: int, radius: int) -> Iterable[int]:
     return sorted(out)
 
 
-def _time_shot(p, c, rec, dobs, img, ws, steps: int) -> float:
+def _time_shot(p, c, rec, dobs, img, ws, steps: int):
     """Milliseconds per stencil step of a checkpointed shot (3 steps per time
-    step: forward, recompute, backward)."""
-    from . import shot
+    step: forward, recompute, backward), and milliseconds per launch of each
+    stencil mode from the library's per-launch timing of a second shot."""
+    from . import reset_stats, set_timing, shot, stats
 
     shot(p, c, rec, dobs, ws, img)  # warm-up
     torch.cuda.synchronize()
@@ -73,7 +75,16 @@ def _time_shot(p, c, rec, dobs, img, ws, steps: int) -> float:
     shot(p, c, rec, dobs, ws, img)
     e1.record()
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / (3 * steps)
+    total = e0.elapsed_time(e1) / (3 * steps)
+    reset_stats()
+    set_timing(True)
+    try:
+        shot(p, c, rec, dobs, ws, img)
+    finally:
+        set_timing(False)
+    per_mode = {k: v["ms"] / v["launches"] for k, v in stats()["stencil"].items()
+                if v["launches"] and v["ms"] > 0}
+    return total, per_mode
 
 
 def tune_stencil(radius: int, padded_shape: Tuple[int, int, int], steps: int = 12,
@@ -100,20 +111,30 @@ def tune_stencil(radius: int, padded_shape: Tuple[int, int, int], steps: int = 1
     rec = torch.zeros((1, 3), dtype=torch.int32, device="cuda")
     dobs = torch.zeros((steps, 1), device="cuda")
     img = torch.zeros((p.nz, p.ny, p.nx), device="cuda")
-    results = {}
+    results, modes = {}, {}
     try:
         for variant in variants:
             for zc in candidates(NZ, radius):
                 try:
                     set_tuning(radius, zc, variant)
-                    results[(variant, zc)] = _time_shot(p, c, rec, dobs, img, ws, steps)
+                    results[(variant, zc)], modes[(variant, zc)] = _time_shot(
+                        p, c, rec, dobs, img, ws, steps)
                 except RtmError:
                     continue  # a variant this driver cannot run
     finally:
         set_tuning(radius, 0, 0)
     best = min(results, key=results.get)
+    # within the best variant, the fastest slab height of each mode (its
+    # launches move different bytes per point and balance differently)
+    per_mode = {}
+    for mode in ("fwd", "fwd_snap", "bwd_image"):
+        t = {zc: m[mode] for (v, zc), m in modes.items() if v == best[0] and mode in m}
+        if t:
+            per_mode[mode] = int(min(t, key=t.get))
     choice = {"zchunk": int(best[1]), "variant": int(best[0]), "ms_per_step": results[best],
-              "trials": {"%d/%d" % k: v for k, v in results.items()}}
+              "zchunk_modes": per_mode,
+              "trials": {"%d/%d" % k: v for k, v in results.items()},
+              "trials_modes": {"%d/%d" % k: v for k, v in modes.items()}}
     with _lock:
         cache = load_cache(cache_path)
         cache[key] = choice
@@ -182,6 +203,10 @@ def apply(radius: int, padded_shape, tune_if_missing: bool = True,
         choice = tune_stencil(radius, padded_shape, cache_path=cache_path)
     if choice is not None:
         set_tuning(radius, int(choice["zchunk"]), int(choice.get("variant", 0)))
+        from . import set_tuning_mode
+
+        for mode, zc in choice.get("zchunk_modes", {}).items():
+            set_tuning_mode(radius, mode, int(zc))
     return choice
 
 

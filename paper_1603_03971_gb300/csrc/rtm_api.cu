@@ -58,6 +58,8 @@ double stability_limit(int r) {
 // ---- tuning, timing and counters ---------------------------------------------
 std::mutex g_mu;
 int g_zchunk[kMaxRadius + 1] = {0};
+// per stencil mode (statistics slot): slab height, 0 = the radius's general one
+int g_zchunk_mode[kMaxRadius + 1][MODE_COUNT] = {{0}};
 int g_variant[kMaxRadius + 1] = {0};
 bool g_timing = false;
 rtm_stats g_stats;
@@ -309,6 +311,7 @@ struct Ctx {
     const float* ae = nullptr;  // codec parameters (learned storage)
     float* illum = nullptr;     // source illumination, model grid (+=), or NULL
     bool snap_padded = false;   // imaging snapshots are padded fields (boundary storage)
+    int zchunk_mode[MODE_COUNT] = {0};  // per-mode slab heights (0: base.zchunk)
 
     float* at(size_t off) const { return reinterpret_cast<float*>(ws + off); }
     float* coarse_slot(size_t k) const {
@@ -365,6 +368,7 @@ rtm_status make_ctx(Ctx& C, const rtm_params* p, const float* c, void* ws, rtm_s
         std::lock_guard<std::mutex> lk(g_mu);
         zc = g_zchunk[p->radius];
         var = g_variant[p->radius];
+        for (int m = 0; m < MODE_COUNT; m++) C.zchunk_mode[m] = g_zchunk_mode[p->radius][m];
     }
     C.base.zchunk = zc > 0 ? zc : auto_zchunk(p->radius, C.d.NX, C.d.NY, C.d.NZ);
     if ((C.d.NZ + C.base.zchunk - 1) / C.base.zchunk > 65535)
@@ -405,6 +409,10 @@ rtm_status stencil(Ctx& C, int mode, const float* cur, float* prev, float* snap,
     // nearly empty last wave)
     if (mode == MODE_REV)
         a.zchunk = auto_zchunk(C.p->radius, a.xend - a.xorg, a.yend - a.yorg, a.zend - a.zorg);
+    // a slab height tuned for this mode (its statistics slot) wins
+    if (C.zchunk_mode[slot] > 0) a.zchunk = C.zchunk_mode[slot];
+    if ((a.zend - a.zorg + a.zchunk - 1) / a.zchunk > 65535)
+        a.zchunk = (a.zend - a.zorg + 65534) / 65535;  // grid.z limit
     a.snap_padded = (mode == MODE_BWD_IMAGE && C.snap_padded) ? 1 : 0;
     bool timing;
     {
@@ -1193,6 +1201,16 @@ rtm_status rtm_set_tuning(int32_t radius, int32_t zchunk, int32_t variant) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_zchunk[radius] = zchunk;
     g_variant[radius] = variant;
+    for (int m = 0; m < MODE_COUNT; m++) g_zchunk_mode[radius][m] = 0;
+    return RTM_OK;
+}
+
+rtm_status rtm_set_tuning_mode(int32_t radius, int32_t mode, int32_t zchunk) {
+    if (radius != 4 && radius != 8) return fail(RTM_ERR_UNSUPPORTED, "radius %d", radius);
+    if (mode < 0 || mode >= MODE_COUNT || mode == 5 || mode == MODE_FWD_SUMSQ || zchunk < 0)
+        return fail(RTM_ERR_INVALID, "mode %d / zchunk %d out of range", mode, zchunk);
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_zchunk_mode[radius][mode] = zchunk;
     return RTM_OK;
 }
 

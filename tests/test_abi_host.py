@@ -67,6 +67,9 @@ def test_valid_params_pass():
     (dict(want_grad=True, image_every=2), 1),
     (dict(storage="boundary", want_grad=True), 1),
     (dict(storage="boundary", nz=8), 1),  # model sides must exceed 2 r = 8
+    (dict(storage="decimated", want_grad=True), 1),
+    (dict(storage="decimated", ckpt_every=41), 1),  # exact window beyond nt
+    (dict(storage="decimated", ckpt_every=-1), 1),
 ])
 def test_invalid_params_rejected(change, code):
     p = _p(**change)

@@ -27,6 +27,19 @@ def test_cache_round_trip(tmp_path):
     assert autotune.load_cache(path) == {}
 
 
+def test_per_mode_slab_heights_are_checked_on_the_host():
+    import paper_1603_03971_gb300 as rtm
+
+    rtm.set_tuning_mode(4, "fwd", 48)
+    rtm.set_tuning_mode(8, "bwd_image", 0)
+    rtm.set_tuning(4, 0, 0)  # clears the per-mode heights of radius 4
+    from paper_1603_03971_gb300 import _lib
+
+    for args in ((5, 0, 16), (4, 5, 16), (4, 7, 16), (4, 0, -1), (4, 9, 16)):
+        with pytest.raises(_lib.RtmError):
+            _lib.call("rtm_set_tuning_mode", *args)
+
+
 @pytest.mark.gpu
 def test_tune_stencil_picks_the_fastest_and_caches(tmp_path):
     path = str(tmp_path / "tune.json")
@@ -34,6 +47,13 @@ def test_tune_stencil_picks_the_fastest_and_caches(tmp_path):
     trials = {tuple(int(x) for x in k.split("/")): v for k, v in choice["trials"].items()}
     assert {v for v, _ in trials} == {1, 2, 3}  # vector loads, TMA 16-row and 8-row tiles
     assert (choice["variant"], choice["zchunk"]) == min(trials, key=trials.get)
+    # the slab height of each mode is the fastest of that mode's launches
+    # within the chosen variant
+    tm = {tuple(int(x) for x in k.split("/")): v for k, v in choice["trials_modes"].items()}
+    assert set(choice["zchunk_modes"]) == {"fwd", "fwd_snap", "bwd_image"}
+    for mode, zc in choice["zchunk_modes"].items():
+        t = {z: m[mode] for (v, z), m in tm.items() if v == choice["variant"]}
+        assert zc == min(t, key=t.get)
     cached = json.load(open(path))
     assert any(v["zchunk"] == choice["zchunk"] for v in cached.values())
     # the second call is served from the cache
