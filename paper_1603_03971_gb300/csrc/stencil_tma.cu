@@ -209,6 +209,7 @@ __device__ __forceinline__ bool bar_poll(uint32_t a, uint32_t parity) {
 __device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, int* abort_flag) {
     if (*reinterpret_cast<volatile int*>(abort_flag)) return false;
     const uint32_t a = s_u32(b);
+    if (bar_poll(a, parity)) return true;  // the common case: the plane is in
     const unsigned long long t0 = wait_now();
     for (long long i = 0; i < kTmaWaitLimit; i++) {
         if (bar_poll(a, parity)) return true;
