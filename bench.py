@@ -237,26 +237,27 @@ def kernel_code_digest(path: str) -> str:
     return hashlib.sha256("\n".join(x for x in lines if x).encode()).hexdigest()
 
 
-def profiled_traffic(radius: int, tile_rows: int, padded_shape):
+def profiled_traffic(radius: int, tile_rows: int, padded_shape, zchunk, alg_bytes):
     """DRAM bytes per launch of the backward imaging stencil from the committed
-    ncu summary, if it was taken on the current kernel source with the same
-    radius and tile and scaled to this padded grid."""
-    if not os.path.exists(PROFILE):
+    ncu summary: its traffic / algorithmic ratio at the run's slab height,
+    times the run's algorithmic bytes per launch; only if the summary was
+    taken on the current kernel code with the same radius, tile rows and
+    padded grid (else None)."""
+    if not os.path.exists(PROFILE) or not zchunk:
         return None
     text = open(PROFILE).read()
-    m_t = re.search(r"traffic_bytes_per_launch:\s*([\d.eE+]+)", text)
     m_h = re.search(r"stencil_code_sha256:\s*([0-9a-f]{64})", text)
     m_r = re.search(r"tile_rows:\s*(\d+)", text)
     m_s = re.search(r"radius:\s*(\d+)", text)
     m_g = re.search(r"padded_grid:\s*([\dx]+)", text)
+    m_t = re.search(r"traffic_ratio_zchunk_%d:\s*([\d.eE+]+)" % int(zchunk), text)
     if not (m_t and m_h and m_r and m_s and m_g) or int(m_r.group(1)) != tile_rows \
             or int(m_s.group(1)) != radius \
             or m_g.group(1) != "x".join(str(int(n)) for n in padded_shape):
         return None
-    cur = kernel_code_digest(STENCIL_SRC)
-    if cur != m_h.group(1):
+    if kernel_code_digest(STENCIL_SRC) != m_h.group(1):
         return None
-    return float(m_t.group(1))
+    return float(m_t.group(1)) * float(alg_bytes)
 
 
 # ----------------------------------------------------------------------------
@@ -923,14 +924,19 @@ def run_ours(args):
     shares = {k: v["ms"] for k, v in st["stencil"].items() if v["launches"]}
     variant = args.variant or (cfg.get("autotune") or {}).get("variant", 0)
     tile_rows = 8 if variant == 3 else 16
+    # slab height of the backward launches: the run's per-mode or general one
+    tuned = cfg.get("autotune") or {}
+    bwd_zchunk = (args.zchunk or (tuned.get("zchunk_modes") or {}).get("bwd_image")
+                  or tuned.get("zchunk"))
     roofline = {
         "kernel": ("k_stencil_tma<%d, MODE_BWD_IMAGE, %d-row tiles>" % (w.radius, tile_rows)
                    if variant != 1 else "k_stencil<%d, MODE_BWD_IMAGE>" % w.radius)
                   + " (backward step + fused zero-lag imaging)",
         "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
         "frac": (achieved / hbm) if achieved else None, "peak_kind": peak_kind,
-        "traffic": (profiled_traffic(w.radius, tile_rows, w.padded_shape)
-                    if variant != 1 else None),
+        "traffic": (profiled_traffic(w.radius, tile_rows, w.padded_shape, bwd_zchunk,
+                                     per_launch_bytes) if variant != 1 else None),
+        "traffic_slab_planes": bwd_zchunk,
         "algorithmic_bytes_per_launch": per_launch_bytes,
         "launch_ms": per_launch_s * 1e3,
         "stencil_ms_per_step": {k: v / args.steps for k, v in shares.items()},
