@@ -463,6 +463,51 @@ rtm_status rtm_batch(const rtm_params *p, int32_t nshots, const rtm_aperture *h_
 rtm_status rtm_forward_noalloc(const rtm_params *p, const float *d_c, const int32_t *d_rec,
                                float *d_data, float *d_u_last, rtm_stream stream);
 
+/* ---- off-grid source and receivers ---------------------------------------
+ * The paper's time step includes "interpolation where necessary" (Sec. II).
+ * Here a source or receiver may sit between grid points: it is spread over
+ * the grid with Kaiser-windowed sinc weights (Hicks 2002): along each axis a
+ * point at xi (cells) weighs grid point i by
+ *   sinc(i - xi) I0(b sqrt(1 - ((i - xi) / 4)^2)) / I0(b),  |i - xi| <= 4,
+ * b = 4.14, on its 8 nearest points (a single point of weight 1 where xi is
+ * a grid point); a tap's weight is the product of its three axis weights.
+ * The source adds c w^n / dx^3 times each tap weight to u^{n+1}; a receiver
+ * records the weighted sum of u^{n+1} over its taps; the receiver pass
+ * injects c g r / dx^3 times each tap weight (the exact transpose). */
+typedef struct rtm_point_taps {
+    int32_t i0, j0, k0;     /* padded index of the first tap along x, y, z */
+    int32_t nx, ny, nz;     /* taps along x, y, z: 1 .. 8 (taps outside the padded
+                               grid are left out) */
+    float wx[8], wy[8], wz[8];  /* the axis weights of those taps */
+    int32_t reserved[2];
+} rtm_point_taps;               /* 128 bytes */
+
+/* Tap tables of a source at h_src_xyz[3] and nrec receivers at
+ * h_rec_xyz[nrec][3], model coordinates in cells (x, y, z; fractional; the
+ * padded position is the model one plus nb), computed on the host in double
+ * precision and stored in float. h_out[0] is the source, h_out[1 + j]
+ * receiver j. Host only. Returns 1 + nrec (entries written only if
+ * out_count >= 1 + nrec), or 0 if a position lies outside the padded grid
+ * or p is invalid. */
+size_t rtm_offgrid_taps(const rtm_params *p, const double *h_src_xyz, int32_t nrec,
+                        const double *h_rec_xyz, rtm_point_taps *h_out, size_t out_count);
+
+/* rtm_forward and rtm_shot with the source and the p->nrec receivers of a
+ * device tap table d_taps[1 + nrec] (from rtm_offgrid_taps) instead of
+ * p->src_* and integer receiver coordinates. Storage: every imaging storage
+ * of rtm_shot (store-all, checkpoints, binomial, boundary, decimated); not
+ * the gradient. The receiver injection of the backward pass adds with
+ * atomics where taps of neighbouring receivers overlap, so its sums are not
+ * ordered. A tap outside the padded grid (a corrupted table) is skipped and
+ * sets RTM_ERR_INVALID in the status word. Costs up to 512 taps per point
+ * and step in the small kernels. */
+rtm_status rtm_forward_offgrid(const rtm_params *p, const float *d_c,
+                               const rtm_point_taps *d_taps, float *d_data, void *d_ws,
+                               size_t ws_bytes, float *d_u_last, rtm_stream stream);
+rtm_status rtm_shot_offgrid(const rtm_params *p, const float *d_c, const rtm_point_taps *d_taps,
+                            const float *d_dobs, float *d_data, void *d_ws, size_t ws_bytes,
+                            float *d_image, rtm_stream stream);
+
 /* ---- X-Y domain decomposition of one shot ----------------------------------
  * The paper's distributed time step (Sec. II): the padded grid is split in x
  * and y into px x py subdomains, each holding its owned block plus an r-wide

@@ -26,7 +26,7 @@ __all__ = [
     "shot", "grad", "misfit", "check", "shot_host", "forward_learned",
     "backward_image_learned", "shot_learned", "snapshot", "set_tuning", "set_timing", "stats",
     "reset_stats", "RtmMisfit", "version", "decomp_plan", "decomp_workspace_size",
-    "forward_decomposed",
+    "forward_decomposed", "offgrid_taps", "forward_offgrid", "shot_offgrid",
 ]
 
 
@@ -230,6 +230,52 @@ def misfit(d, obs, resid=None, J=None, stream=None):
     call("rtm_misfit", _dev(d, name="d"), _dev(obs, name="obs"), ctypes.c_int64(d.numel()),
          _dev(resid, name="resid"), _dev(J, torch.float64, "J"), _stream(stream))
     return J, resid
+
+
+TAP_BYTES = 128  # sizeof(rtm_point_taps)
+
+
+def offgrid_taps(p: RtmParams, src_xyz, rec_xyz, device=None) -> torch.Tensor:
+    """Tap tables (Kaiser-windowed sinc weights) of a source and receivers at
+    fractional model coordinates (x, y, z), computed by the library on the
+    host: a uint8 tensor of (1 + nrec) x 128 bytes (entry 0 the source), on
+    ``device`` if given."""
+    import numpy as np
+
+    src = np.ascontiguousarray(src_xyz, dtype=np.float64).reshape(3)
+    rec = np.ascontiguousarray(rec_xyz, dtype=np.float64).reshape(-1, 3)
+    n = 1 + rec.shape[0]
+    out = np.zeros(n * TAP_BYTES, dtype=np.uint8)
+    got = lib().rtm_offgrid_taps(ctypes.byref(p), src.ctypes.data_as(ctypes.c_void_p),
+                                 rec.shape[0], rec.ctypes.data_as(ctypes.c_void_p),
+                                 out.ctypes.data_as(ctypes.c_void_p), n)
+    if got != n:
+        raise RtmError(1, "rtm_offgrid_taps", (lib().rtm_last_error() or b"").decode())
+    t = torch.from_numpy(out)
+    return t.to(device) if device is not None else t
+
+
+def _taps(t: torch.Tensor, p: RtmParams):
+    if not t.is_cuda or t.dtype != torch.uint8 or t.numel() != (1 + p.nrec) * TAP_BYTES:
+        raise ValueError("tap table must be a CUDA uint8 tensor of (1 + nrec) x 128 bytes")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def forward_offgrid(p: RtmParams, c, taps, ws, data=None, u_last=None, stream=None):
+    """Forward modelling with the off-grid source and receivers of a tap table."""
+    w, wb = _ws(ws)
+    call("rtm_forward_offgrid", ctypes.byref(p), _dev(c, name="c"), _taps(taps, p),
+         _dev(data, name="data"), w, wb, _dev(u_last, name="u_last"), _stream(stream))
+    return data, u_last
+
+
+def shot_offgrid(p: RtmParams, c, taps, dobs, ws, image, data=None, stream=None):
+    """RTM shot (image +=) with the off-grid source and receivers of a tap table."""
+    w, wb = _ws(ws)
+    call("rtm_shot_offgrid", ctypes.byref(p), _dev(c, name="c"), _taps(taps, p),
+         _dev(dobs, name="dobs"), _dev(data, name="data"), w, wb, _dev(image, name="image"),
+         _stream(stream))
+    return image
 
 
 def decomp_plan(p: RtmParams, px: int, py: int):

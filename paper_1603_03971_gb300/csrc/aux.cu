@@ -25,14 +25,6 @@ __device__ __forceinline__ long long rec_index(const Geometry& G, const int32_t*
     return ((long long)z * G.NY + y) * G.NX + x;
 }
 
-__device__ __forceinline__ float sponge_at(const Geometry& G, const float* gx, const float* gy,
-                                           const float* gz, long long i) {
-    const long long plane = (long long)G.NX * G.NY;
-    const int z = (int)(i / plane);
-    const int y = (int)((i % plane) / G.NX);
-    const int x = (int)(i % G.NX);
-    return gx[x] * gy[y] * gz[z];
-}
 
 // Cerjan-type profile: exp(-(0.015 (nb - d))^2) within nb cells of a face
 __device__ __forceinline__ float sponge_1d(int i, int n, int nb) {

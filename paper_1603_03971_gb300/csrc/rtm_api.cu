@@ -312,6 +312,7 @@ struct Ctx {
     float* illum = nullptr;     // source illumination, model grid (+=), or NULL
     bool snap_padded = false;   // imaging snapshots are padded fields (boundary storage)
     int zchunk_mode[MODE_COUNT] = {0};  // per-mode slab heights (0: base.zchunk)
+    const rtm_point_taps* taps = nullptr;  // off-grid source and receivers, or NULL
 
     float* at(size_t off) const { return reinterpret_cast<float*>(ws + off); }
     float* coarse_slot(size_t k) const {
@@ -447,17 +448,26 @@ rtm_status prepare_tables(Ctx& C) {
 
 rtm_status fwd_aux(Ctx& C, const float* cur, float* prev, const int32_t* rec, float* data_row,
                    const float* w_n) {
-    CU(launch_fwd_aux(C.G, cur, prev, C.base.c, C.base.gx, C.base.gy, C.base.gz, rec,
-                      C.p->nrec, data_row, C.src, w_n, C.inv_dx3, C.status(), C.s));
+    if (C.taps)
+        CU(launch_fwd_aux_off(C.G, cur, prev, C.base.c, C.base.gx, C.base.gy, C.base.gz, C.taps,
+                              C.p->nrec, data_row, w_n, C.inv_dx3, C.status(), C.s));
+    else
+        CU(launch_fwd_aux(C.G, cur, prev, C.base.c, C.base.gx, C.base.gy, C.base.gz, rec,
+                          C.p->nrec, data_row, C.src, w_n, C.inv_dx3, C.status(), C.s));
     count_launch();
     return RTM_OK;
 }
 
 rtm_status bwd_aux(Ctx& C, const float* mcur, float* mprev, const int32_t* rec,
                    const float* r_row, float* src_adj_slot, float* grad_acc, const float* w_n) {
-    CU(launch_bwd_aux(C.G, mcur, mprev, C.base.c, C.base.gx, C.base.gy, C.base.gz, rec,
-                      C.p->nrec, r_row, C.src, src_adj_slot, grad_acc, w_n, C.inv_dx3,
-                      C.status(), C.s));
+    if (C.taps)  // imaging only: no gradient source term
+        CU(launch_bwd_aux_off(C.G, mcur, mprev, C.base.c, C.base.gx, C.base.gy, C.base.gz,
+                              C.taps, C.p->nrec, r_row, src_adj_slot, C.inv_dx3, C.status(),
+                              C.s));
+    else
+        CU(launch_bwd_aux(C.G, mcur, mprev, C.base.c, C.base.gx, C.base.gy, C.base.gz, rec,
+                          C.p->nrec, r_row, C.src, src_adj_slot, grad_acc, w_n, C.inv_dx3,
+                          C.status(), C.s));
     count_launch();
     return RTM_OK;
 }
@@ -918,6 +928,47 @@ rtm_status rtm_shot(const rtm_params* p, const float* d_c, const int32_t* d_rec,
     CHECK(make_ctx(C, p, d_c, d_ws, stream));
     CHECK(run_forward(C, d_rec, d_data, nullptr));
     CHECK(run_backward(C, d_rec, d_dobs, nullptr, false));
+    CU(launch_image_finalize(C.G, C.at(C.L.img), d_image, C.s));
+    count_launch();
+    return finish(C);
+}
+
+static rtm_status offgrid_checks(const rtm_params* p, const float* d_c,
+                                 const rtm_point_taps* d_taps, void* d_ws, size_t ws_bytes) {
+    // the receivers come from the tap table: common_checks with a stand-in
+    // receiver pointer
+    CHECK(common_checks(p, d_c, reinterpret_cast<const int32_t*>(d_taps), d_ws, ws_bytes));
+    if (!d_taps) return fail(RTM_ERR_INVALID, "tap table is NULL");
+    if ((uintptr_t)d_taps % 16) return fail(RTM_ERR_INVALID, "tap table not 16-byte aligned");
+    if (p->want_grad)
+        return fail(RTM_ERR_STATE, "off-grid points serve modelling and imaging, not the gradient");
+    if (p->storage == RTM_STORE_LEARNED)
+        return fail(RTM_ERR_STATE, "off-grid points are not available with learned storage");
+    return RTM_OK;
+}
+
+rtm_status rtm_forward_offgrid(const rtm_params* p, const float* d_c,
+                               const rtm_point_taps* d_taps, float* d_data, void* d_ws,
+                               size_t ws_bytes, float* d_u_last, rtm_stream stream) {
+    CHECK(offgrid_checks(p, d_c, d_taps, d_ws, ws_bytes));
+    Ctx C;
+    CHECK(make_ctx(C, p, d_c, d_ws, stream));
+    C.taps = d_taps;
+    CHECK(run_forward(C, nullptr, d_data, d_u_last));
+    return finish(C);
+}
+
+rtm_status rtm_shot_offgrid(const rtm_params* p, const float* d_c, const rtm_point_taps* d_taps,
+                            const float* d_dobs, float* d_data, void* d_ws, size_t ws_bytes,
+                            float* d_image, rtm_stream stream) {
+    CHECK(offgrid_checks(p, d_c, d_taps, d_ws, ws_bytes));
+    if (!d_dobs && p->nrec > 0) return fail(RTM_ERR_INVALID, "observed data is NULL");
+    if (!d_image) return fail(RTM_ERR_INVALID, "image is NULL");
+    Ctx C;
+    CHECK(make_ctx(C, p, d_c, d_ws, stream));
+    C.taps = d_taps;
+    CHECK(run_forward(C, nullptr, d_data, nullptr));
+    CHECK(run_backward(C, nullptr, d_dobs, nullptr, false));
     CU(launch_image_finalize(C.G, C.at(C.L.img), d_image, C.s));
     count_launch();
     return finish(C);

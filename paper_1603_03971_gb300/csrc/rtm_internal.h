@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+struct rtm_point_taps;  // include/rtm.h
+
 namespace rtm {
 
 // Stencil kernel modes. All of them compute the same leapfrog update
@@ -88,6 +90,16 @@ struct Geometry {
     int NX, NY, NZ, nb, nx, ny, nz;
 };
 
+// sponge factor g = gx gy gz of padded cell i
+__device__ __forceinline__ float sponge_at(const Geometry& G, const float* gx, const float* gy,
+                                           const float* gz, long long i) {
+    const long long plane = (long long)G.NX * G.NY;
+    const int z = (int)(i / plane);
+    const int y = (int)((i % plane) / G.NX);
+    const int x = (int)(i % G.NX);
+    return gx[x] * gy[y] * gz[z];
+}
+
 cudaError_t launch_sponge(const Geometry& G, float* gx, float* gy, float* gz, cudaStream_t s);
 cudaError_t launch_wavelet(int nt, double dt, double f0, double t0, float* w, cudaStream_t s);
 cudaError_t launch_model_prep(const Geometry& G, const float* vel, int squared, double dt,
@@ -119,6 +131,19 @@ cudaError_t launch_misfit(const float* d, const float* obs, long long n, float* 
 // reconstruct the model region of a snapshot slab by linear interpolation
 cudaError_t launch_decimate(const Geometry& G, const float* u, float* coarse, cudaStream_t s);
 cudaError_t launch_upsample(const Geometry& G, const float* coarse, float* slab, cudaStream_t s);
+// off-grid source and receivers (offgrid.cu): the same steps as
+// launch_fwd_aux / launch_bwd_aux with each point spread over its tap table
+// (taps[0] the source, taps[1 .. nrec] the receivers)
+cudaError_t launch_fwd_aux_off(const Geometry& G, const float* u_cur, float* u_prev,
+                               const float* c, const float* gx, const float* gy,
+                               const float* gz, const rtm_point_taps* taps, int nrec,
+                               float* data_row, const float* w_n, float inv_dx3, int* status,
+                               cudaStream_t s);
+cudaError_t launch_bwd_aux_off(const Geometry& G, const float* mu_cur, float* mu_prev,
+                               const float* c, const float* gx, const float* gy,
+                               const float* gz, const rtm_point_taps* taps, int nrec,
+                               const float* r_row, float* src_adj_slot, float inv_dx3,
+                               int* status, cudaStream_t s);
 // post-run check: any non-finite value among n floats sets *status to
 // RTM_ERR_NUMERIC (unless another error is already recorded)
 cudaError_t launch_finite_scan(const float* f, long long n, int* status, cudaStream_t s);
