@@ -78,6 +78,8 @@ def parse():
                     help="skip the two-layer 64^3 full-RTM leg (per-shot time, CUDA graph)")
     ap.add_argument("--no-r8", action="store_true",
                     help="skip the radius-8 leg (smooth 512^3 model, 200 steps)")
+    ap.add_argument("--no-decomp", action="store_true",
+                    help="skip the 2 x 2 domain-decomposition leg (smooth 512^3 forward)")
     ap.add_argument("--batch-nt", type=int, default=1500)
     ap.add_argument("--batch-shots", default="all",
                     help="comma-separated aperture indices of the batched workload (default all 32)")
@@ -802,6 +804,49 @@ def r8_leg(dev, hbm):
             "stencil_modes": modes, "tuning": tuned}
 
 
+def decomp_leg(dev, px=2, py=2, nt=200):
+    """The single-shot workload's forward modelling (576^3 padded, radius 4,
+    200 steps) on a px x py X-Y decomposition with overlapped halo exchange,
+    against the same forward pass on one domain (same tile, CUDA events)."""
+    import torch
+
+    import paper_1603_03971_gb300 as rtm
+    import rtm_inputs
+
+    w = rtm_inputs.WORKLOADS["smooth_512"].scaled(nt=nt)
+    tune_shape(w.radius, w.padded_shape)
+    p = rtm.params_for(w, storage="all", image_every=nt)
+    ws = rtm.alloc_workspace(p, dev)
+    c = rtm.model_prep(p, w.velocity_model(device=dev).contiguous(), ws)
+    rec = torch.from_numpy(w.receivers()).to(dev)
+    data = torch.empty((nt, p.nrec), dtype=torch.float32, device=dev)
+    wsd = torch.empty(rtm.decomp_workspace_size(p, px, py), dtype=torch.uint8, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        fn()  # warm-up
+        torch.cuda.synchronize()
+        ev[0].record()
+        fn()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / 1e3
+
+    t1 = timed(lambda: rtm.forward(p, c, rec, ws, data=data))
+    ref = data.clone()
+    td = timed(lambda: rtm.forward_decomposed(p, px, py, c, rec, wsd, data=data))
+    rtm.check(wsd)
+    same = bool(torch.equal(data, ref))
+    NZ, NY, NX = w.padded_shape
+    del ws, wsd
+    return {"workload": "smooth_512 forward modelling, %d steps, %d x %d subdomains" % (nt, px, py),
+            "forward_s_one_domain": t1, "forward_s_decomposed": td,
+            "gpoint_updates_per_s_decomposed": nt * NX * NY * NZ / td / 1e9,
+            "overhead": td / t1 - 1.0, "data_bitwise_equal": same,
+            "note": "all subdomains on one GPU; the exchange is device copies on a "
+                    "communication stream"}
+
+
 def batch_leg(args, dev):
     """32 shots on seeded uneven apertures of a 1024 x 1024 x 512 layered /
     salt model, radius-8 stencil, each a full checkpointed RTM, in one
@@ -1025,6 +1070,11 @@ def run_ours(args):
         ws = None
         torch.cuda.empty_cache()
         small_res = small_leg(dev)
+    decomp_res = None
+    if rank == 0 and not args.no_decomp:
+        ws = None
+        torch.cuda.empty_cache()
+        decomp_res = decomp_leg(dev)
     r8_res = None
     if rank == 0 and not args.no_r8:
         ws = None
@@ -1052,7 +1102,7 @@ def run_ours(args):
             "config": cfg, "shot_s": t_max / args.steps, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": st["launches"],
             "clocks": clocks, "impl": "ours", "learned": learned, "batch": batch_res,
-            "two_layer_64": small_res, "radius8": r8_res,
+            "two_layer_64": small_res, "radius8": r8_res, "decomposition": decomp_res,
             "imaging": imaging_res, "revolve": revolve_res, "boundary": boundary_res,
             "gradient": grad_res,
             # the paper's own reported improvements (relative speedups of a CPU
