@@ -457,7 +457,8 @@ rtm_status rtm_batch(const rtm_params *p, int32_t nshots, const rtm_aperture *h_
  * outside the padded grid get zero traces and are not reported (there is no
  * workspace for rtm_check). It does not update rtm_stats. It always runs the
  * 16-byte vector-load stencil kernel (the plane-load variant of
- * rtm_set_tuning does not apply); the slab height set by rtm_set_tuning does.
+ * rtm_set_tuning does not apply); the forward slab height set by
+ * rtm_set_tuning or rtm_set_tuning_mode (mode 0) does.
  * A failed CUDA call returns RTM_ERR_CUDA with its message in
  * rtm_last_error(). */
 rtm_status rtm_forward_noalloc(const rtm_params *p, const float *d_c, const int32_t *d_rec,
@@ -546,7 +547,10 @@ size_t rtm_decomp_workspace_size(const rtm_params *p, int32_t px, int32_t py);
  * with the same tile bit for bit. A receiver outside the padded grid gets a
  * zero trace and sets RTM_ERR_INVALID in the status word (rtm_check on
  * d_ws); the post-run scan of u^nt applies. The call creates and destroys
- * one stream and two events of its own. */
+ * streams and events of its own: up to eight compute streams (subdomain k
+ * on stream k % 8, so that the subdomains' launches overlap) and the
+ * communication stream; the caller's stream waits for all of them before
+ * the call returns. */
 rtm_status rtm_forward_decomposed(const rtm_params *p, int32_t px, int32_t py, const float *d_c,
                                   const int32_t *d_rec, float *d_data, void *d_ws,
                                   size_t ws_bytes, float *d_u_last, rtm_stream stream);

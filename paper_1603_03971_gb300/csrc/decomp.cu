@@ -19,10 +19,12 @@
 // The star stencil reads along the axes only, so the corner blocks of the
 // halo are never read and never exchanged.
 //
-// Each step of subdomain s on the compute stream: the source pre-adjust and
-// receiver gather (as in the single-domain forward pass); the band launches
-// (tiles within 64 columns or 16 rows of a face that has a neighbour, which
-// contain every cell the neighbours need); an event; the interior launch.
+// Each step of subdomain s on its compute stream (up to eight streams, so
+// that the subdomains' launches overlap on the GPU as their ranks' would):
+// the source pre-adjust and receiver gather (as in the single-domain forward
+// pass); the band launches (tiles within 64 columns or 16 rows of a face that
+// has a neighbour, which contain every cell the neighbours need); an event;
+// the interior launch.
 // On the communication stream, after that event: one pack kernel gathers the
 // r-wide strips of every subdomain into its send buffer, one copy per face
 // moves each strip into the neighbour's receive buffer, one unpack kernel
@@ -208,14 +210,24 @@ void strip_rect(const Sub& s, int r, int face, bool halo, int* q) {
                                          cudaGetErrorString(e_));                      \
     } while (0)
 
-// owns the communication stream and its events for one call
-struct CommStream {
-    cudaStream_t st = nullptr;
-    cudaEvent_t band = nullptr, done = nullptr;
-    ~CommStream() {
+constexpr int kMaxStreams = 8;  // compute streams; subdomain k runs on stream k % n
+
+// the compute streams (subdomains' launches overlap, as their ranks' would),
+// the communication stream and their events, owned by one call
+struct Streams {
+    int n = 0;
+    cudaStream_t comp[kMaxStreams] = {nullptr};
+    cudaEvent_t band[kMaxStreams] = {nullptr};  // a compute stream's band launches are done
+    cudaStream_t comm = nullptr;
+    cudaEvent_t start = nullptr, done = nullptr;  // set-up done; a step's exchange done
+    ~Streams() {
+        for (int i = 0; i < n; i++) {
+            if (band[i]) cudaEventDestroy(band[i]);
+            if (comp[i]) cudaStreamDestroy(comp[i]);
+        }
         if (done) cudaEventDestroy(done);
-        if (band) cudaEventDestroy(band);
-        if (st) cudaStreamDestroy(st);
+        if (start) cudaEventDestroy(start);
+        if (comm) cudaStreamDestroy(comm);
     }
 };
 
@@ -387,7 +399,7 @@ rtm_status rtm_forward_decomposed(const rtm_params* p, int32_t px, int32_t py, c
     // ---- launch shapes
     const int var = tuning_variant(r);
     const int tile_rows = var == 2 ? 16 : 8;
-    const int zc_set = tuning_zchunk(r);
+    const int zc_set = tuning_zchunk(r, MODE_FWD);
     std::vector<StepArgs> base(nsub);
     for (int k = 0; k < nsub; k++) {
         const Sub& s = P.sub[k];
@@ -429,6 +441,19 @@ rtm_status rtm_forward_decomposed(const rtm_params* p, int32_t px, int32_t py, c
         if (bn > 0 && xr > xl) band[k].push_back({xl, xr, r + s.oy - bn, r + s.oy});
         inner[k] = {xl, xr, yl, yr};
     }
+    Streams C;
+    C.n = std::min(nsub, kMaxStreams);
+    for (int i = 0; i < C.n; i++) {
+        DCU(cudaStreamCreateWithFlags(&C.comp[i], cudaStreamNonBlocking));
+        DCU(cudaEventCreateWithFlags(&C.band[i], cudaEventDisableTiming));
+    }
+    DCU(cudaStreamCreateWithFlags(&C.comm, cudaStreamNonBlocking));
+    DCU(cudaEventCreateWithFlags(&C.start, cudaEventDisableTiming));
+    DCU(cudaEventCreateWithFlags(&C.done, cudaEventDisableTiming));
+    DCU(cudaEventRecord(C.start, S));  // the set-up above
+    for (int i = 0; i < C.n; i++) DCU(cudaStreamWaitEvent(C.comp[i], C.start, 0));
+    DCU(cudaStreamWaitEvent(C.comm, C.start, 0));
+    auto stream_of = [&](int k) { return C.comp[k % C.n]; };
     auto launch = [&](int k, const Rect& q, float* cur, float* prev) -> cudaError_t {
         if (q.x1 <= q.x0 || q.y1 <= q.y0) return cudaSuccess;
         StepArgs a = base[k];
@@ -438,13 +463,8 @@ rtm_status rtm_forward_decomposed(const rtm_params* p, int32_t px, int32_t py, c
         a.xend = q.x1;
         a.yorg = q.y0;
         a.yend = q.y1;
-        return launch_stencil_tma(r, MODE_FWD, a, status, S, tile_rows);
+        return launch_stencil_tma(r, MODE_FWD, a, status, stream_of(k), tile_rows);
     };
-
-    CommStream C;
-    DCU(cudaStreamCreateWithFlags(&C.st, cudaStreamNonBlocking));
-    DCU(cudaEventCreateWithFlags(&C.band, cudaEventDisableTiming));
-    DCU(cudaEventCreateWithFlags(&C.done, cudaEventDisableTiming));
     const int npack = (int)hs.size() / 2;
     size_t max_strip = 1;
     for (const HaloStrip& h : hs) max_strip = std::max(max_strip, (size_t)h.w * h.h * h.NZ);
@@ -455,7 +475,8 @@ rtm_status rtm_forward_decomposed(const rtm_params* p, int32_t px, int32_t py, c
     // ---- the time loop
     for (int n = 0; n < p->nt; n++) {
         const int wn = n % 2;  // the new field u^{n+1} lands in f[wn]
-        if (n > 0) DCU(cudaStreamWaitEvent(S, C.done, 0));  // halos of u^n are in
+        if (n > 0)  // halos of u^n are in
+            for (int i = 0; i < C.n; i++) DCU(cudaStreamWaitEvent(C.comp[i], C.done, 0));
         for (int k = 0; k < nsub; k++) {
             const Sub& s = P.sub[k];
             if (s.nrec == 0 && s.src < 0) continue;
@@ -466,14 +487,16 @@ rtm_status rtm_forward_decomposed(const rtm_params* p, int32_t px, int32_t py, c
             DCU(launch_fwd_aux(Gl, F(s.f[1 - wn]), F(s.f[wn]), F(s.c), F(s.gx), F(s.gy),
                                F(P.gz), d_lrec + 3 * (size_t)s.rec0, s.nrec, row,
                                s.src >= 0 ? s.src : 0, s.src >= 0 ? F(P.wavelet) + n : nullptr,
-                               inv_dx3, status, S));
+                               inv_dx3, status, stream_of(k)));
         }
         for (int k = 0; k < nsub; k++)
             for (const Rect& q : band[k]) DCU(launch(k, q, F(P.sub[k].f[1 - wn]), F(P.sub[k].f[wn])));
-        DCU(cudaEventRecord(C.band, S));
+        for (int i = 0; i < C.n; i++) {
+            DCU(cudaEventRecord(C.band[i], C.comp[i]));
+            DCU(cudaStreamWaitEvent(C.comm, C.band[i], 0));
+        }
         if (npack > 0) {
-            DCU(cudaStreamWaitEvent(C.st, C.band, 0));
-            k_halo_copy<<<dim3(gx_blocks, npack), 256, 0, C.st>>>(d_strips, wn, 0);
+            k_halo_copy<<<dim3(gx_blocks, npack), 256, 0, C.comm>>>(d_strips, wn, 0);
             DCU(cudaGetLastError());
             for (int k = 0; k < nsub; k++) {
                 const Sub& s = P.sub[k];
@@ -483,15 +506,21 @@ rtm_status rtm_forward_decomposed(const rtm_params* p, int32_t px, int32_t py, c
                     const Sub& d = P.sub[t];
                     const int g = f ^ 1;  // the face of t that looks back at s
                     DCU(cudaMemcpyAsync(F(d.recv) + strip_offset(d, g), F(s.send) + strip_offset(s, f),
-                                        sizeof(float) * s.strip[f], cudaMemcpyDeviceToDevice, C.st));
+                                        sizeof(float) * s.strip[f], cudaMemcpyDeviceToDevice,
+                                        C.comm));
                 }
             }
-            k_halo_copy<<<dim3(gx_blocks, npack), 256, 0, C.st>>>(d_strips + npack, wn, 1);
+            k_halo_copy<<<dim3(gx_blocks, npack), 256, 0, C.comm>>>(d_strips + npack, wn, 1);
             DCU(cudaGetLastError());
         }
-        DCU(cudaEventRecord(C.done, C.st));
+        DCU(cudaEventRecord(C.done, C.comm));
         for (int k = 0; k < nsub; k++)
             DCU(launch(k, inner[k], F(P.sub[k].f[1 - wn]), F(P.sub[k].f[wn])));
+    }
+    // the caller's stream continues after every compute stream and the last exchange
+    for (int i = 0; i < C.n; i++) {
+        DCU(cudaEventRecord(C.band[i], C.comp[i]));
+        DCU(cudaStreamWaitEvent(S, C.band[i], 0));
     }
     DCU(cudaStreamWaitEvent(S, C.done, 0));
     // u^{nt} is in f[(nt - 1) % 2], u^{nt - 1} in f[nt % 2]

@@ -811,9 +811,11 @@ void rtm::step_weights(int r, double dx, float* out) {
     for (int k = 1; k <= r; k++) out[k] = (float)(a[k] * inv_dx2);
 }
 
-int rtm::tuning_zchunk(int radius) {
+int rtm::tuning_zchunk(int radius, int mode) {
     if (radius < 0 || radius > kMaxRadius) return 0;
     std::lock_guard<std::mutex> lk(g_mu);
+    if (mode >= 0 && mode < MODE_COUNT && g_zchunk_mode[radius][mode] > 0)
+        return g_zchunk_mode[radius][mode];
     return g_zchunk[radius];
 }
 

@@ -170,7 +170,8 @@ cudaError_t launch_image_laplacian(const float* image, int nx, int ny, int nz,
 int set_error(int code, const char* fmt, ...);
 // plane-load variant chosen by rtm_set_tuning for a radius (0: automatic)
 int tuning_variant(int radius);
-// z-slab height chosen by rtm_set_tuning for a radius (0: automatic)
-int tuning_zchunk(int radius);
+// z-slab height chosen by rtm_set_tuning for a radius (0: automatic); with a
+// mode, that mode's height from rtm_set_tuning_mode where one is set
+int tuning_zchunk(int radius, int mode = -1);
 
 }  // namespace rtm

@@ -134,7 +134,7 @@ extern "C" rtm_status rtm_forward_noalloc(const rtm_params* p, const float* d_c,
     A.nz = p->nz;
     // the slab height set by rtm_set_tuning applies; the plane loads are
     // always the vector-load kernel's
-    const int zc = tuning_zchunk(p->radius);
+    const int zc = tuning_zchunk(p->radius, MODE_FWD);
     A.zchunk = zc > 0 ? zc : auto_zchunk(p->radius, NX, NY, NZ);
     if ((NZ + A.zchunk - 1) / A.zchunk > 65535) A.zchunk = (NZ + 65534) / 65535;
     set_region(A, MODE_FWD);
