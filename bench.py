@@ -84,6 +84,9 @@ def parse():
     ap.add_argument("--batch-shots", default="all",
                     help="comma-separated aperture indices of the batched workload (default all 32)")
     ap.add_argument("--batch-ckpt", type=int, default=50, help="checkpoint interval of the batch")
+    ap.add_argument("--batch-compare-nt", type=int, default=100,
+                    help="steps of the comparison of the batch with single shots on the same "
+                         "apertures (0: skip)")
     ap.add_argument("--imaging", action="store_true",
                     help="also time the imaging-condition variants (source illumination, "
                          "normalised and Laplacian-filtered image) on the main workload")
@@ -892,16 +895,69 @@ def batch_leg(args, dev):
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3
     rtm.check(ws)
-    rtm.set_tuning(p.radius, 0, 0)
     pts = sum((a.nx + 2 * p.nb) * (a.ny + 2 * p.nb) * (a.nz + 2 * p.nb) for a in aps)
     updates = 3 * nt * pts
+    ws_gb = ws.numel() / 1e9
+    del ws, dobs
+    torch.cuda.empty_cache()
+    # the same apertures as single shots, one after another, against the
+    # batch over a shorter run: the batch's own rate relative to the
+    # single-shot kernel at the apertures' sizes
+    same = None
+    if args.batch_compare_nt > 0:
+        nc = args.batch_compare_nt
+        pc = p.copy(nt=nc)
+        wsb = B.alloc_workspace(pc, aps, budget, device=dev)
+        dc = torch.zeros(B.data_size(pc, aps), dtype=torch.float32, device=dev)
+        B.run(pc, aps, vel, dc, img, wsb, budget=budget, zchunk=zchunk)  # warm-up
+        torch.cuda.synchronize()
+        e0.record()
+        B.run(pc, aps, vel, dc, img, wsb, budget=budget, zchunk=zchunk)
+        e1.record()
+        torch.cuda.synchronize()
+        rtm.check(wsb)
+        t_b = e0.elapsed_time(e1) / 1e3
+        del wsb, dc
+        torch.cuda.empty_cache()
+        single = []
+        for a in aps:
+            q = rtm.make_params(a.nx, a.ny, a.nz, p.nb, p.radius, nc, p.dx, p.dt, p.f0, p.t0,
+                                (a.src_x, a.src_y, a.src_z), a.nx * a.ny, storage="ckpt",
+                                ckpt_every=p.ckpt_every)
+            single.append(q)
+        ws_s = torch.empty(max(rtm.workspace_size(q) for q in single), dtype=torch.uint8,
+                           device=dev)
+        cs, recs, ds = [], [], []
+        for a, q in zip(aps, single):
+            v = vel[a.oz:a.oz + a.nz, a.oy:a.oy + a.ny, a.ox:a.ox + a.nx].contiguous()
+            cs.append(rtm.model_prep(q, v, ws_s))
+            recs.append(torch.from_numpy(rtm_inputs.surface_receivers(a.nx, a.ny, a.rec_z)).to(dev))
+            ds.append(torch.zeros((nc, q.nrec), dtype=torch.float32, device=dev))
+        ims = [torch.zeros((a.nz, a.ny, a.nx), dtype=torch.float32, device=dev) for a in aps]
+        for q, cc, rr, dd, im in list(zip(single, cs, recs, ds, ims))[:2]:  # warm-up
+            rtm.shot(q, cc, rr, dd, ws_s, im)
+        torch.cuda.synchronize()
+        e0.record()
+        for q, cc, rr, dd, im in zip(single, cs, recs, ds, ims):
+            rtm.shot(q, cc, rr, dd, ws_s, im)
+        e1.record()
+        torch.cuda.synchronize()
+        rtm.check(ws_s)
+        t_s = e0.elapsed_time(e1) / 1e3
+        del ws_s, cs, ds, ims
+        u_c = 3 * nc * pts
+        same = {"steps": nc, "batch_s": t_b, "single_shots_s": t_s,
+                "batch_gpoint_updates_per_s": u_c / t_b / 1e9,
+                "single_gpoint_updates_per_s": u_c / t_s / 1e9,
+                "batch_over_single": t_s / t_b}
+    rtm.set_tuning(p.radius, 0, 0)
     shots = ("32 shots" if args.batch_shots == "all"
              else "shots %s of the 32" % args.batch_shots)
     return {"workload": "%s, apertures 128-384 x 128-384 x 256-512 of a 1024x1024x512 "
                         "layered/salt model, r=8, %d steps, checkpoint every %d"
                         % (shots, nt, args.batch_ckpt),
             "seconds": t, "gpoint_updates_per_s": updates / t / 1e9, "updates": updates,
-            "workspace_gb": ws.numel() / 1e9,
+            "workspace_gb": ws_gb, "same_apertures_as_single_shots": same,
             "variant": args.variant or (tuned["variant"] if tuned else 0),
             "tuning": None if tuned is None else {
                 "tile_rows": 8 if tuned["variant"] == 3 else 16, "zchunk": tuned["zchunk"],

@@ -399,7 +399,7 @@ rtm_status rtm_forward_decomposed(const rtm_params* p, int32_t px, int32_t py, c
     // ---- launch shapes
     const int var = tuning_variant(r);
     const int tile_rows = var == 2 ? 16 : 8;
-    const int zc_set = tuning_zchunk(r, MODE_FWD);
+    const int zc_set = tuning_zchunk(r);
     std::vector<StepArgs> base(nsub);
     for (int k = 0; k < nsub; k++) {
         const Sub& s = P.sub[k];
