@@ -4,6 +4,8 @@
 
 #include <math.h>
 
+#include <algorithm>
+
 #include "band.cuh"
 #include "rtm_internal.h"
 
@@ -315,16 +317,15 @@ __global__ void k_finite_scan(const float* __restrict__ f, long long n, int vec,
 
 // decimated storage, coding: keep every other sample of the model region
 // on each axis, coarse[kz][ky][kx] = u[nb + 2 kz][nb + 2 ky][nb + 2 kx] of a
-// padded field; coarse sides are (n + 1) / 2
+// padded field; coarse sides are (n + 1) / 2. A block walks coarse rows
+// (ky, kz), its threads along x
 __global__ void k_decimate(Geometry G, const float* __restrict__ u, float* __restrict__ coarse,
                            int cx, int cy, int cz) {
-    const long long n = (long long)cx * cy * cz;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int kx = (int)(i % cx);
-        const int ky = (int)((i / cx) % cy);
-        const int kz = (int)(i / ((long long)cx * cy));
-        coarse[i] = u[((long long)(G.nb + 2 * kz) * G.NY + (G.nb + 2 * ky)) * G.NX + G.nb + 2 * kx];
+    for (int row = blockIdx.x; row < cy * cz; row += gridDim.x) {
+        const int ky = row % cy, kz = row / cy;
+        const float* src = u + ((long long)(G.nb + 2 * kz) * G.NY + (G.nb + 2 * ky)) * G.NX + G.nb;
+        float* dst = coarse + (long long)row * cx;
+        for (int kx = threadIdx.x; kx < cx; kx += blockDim.x) dst[kx] = __ldcs(src + 2 * kx);
     }
 }
 
@@ -338,34 +339,66 @@ __device__ __forceinline__ void lin_axis(int j, int nc, int& i0, float& w1) {
 
 // decimated storage, decoding: linear interpolation along each axis back to
 // the model region of a snapshot slab [nz][ny][NX] (columns nb .. nb + nx);
-// the weights (1, 1/2, 1/4, 1/8) are exact, and the corners are summed in a
-// fixed order
+// the weights (1, 1/2) are exact. One warp per output row (y, z): each lane
+// interpolates one kept column along y and z from the four coarse rows
+// (coalesced loads), takes its right neighbour's value by a shuffle, and
+// writes the even output sample (the kept column) and the odd one (the mean
+// of the two, or a copy past the last kept column)
 __global__ void k_upsample(Geometry G, const float* __restrict__ coarse, int cx, int cy, int cz,
                            float* __restrict__ slab) {
-    const long long n = (long long)G.nx * G.ny * G.nz;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int x = (int)(i % G.nx);
-        const int y = (int)((i / G.nx) % G.ny);
-        const int z = (int)(i / ((long long)G.nx * G.ny));
-        int x0, y0, z0;
-        float wx, wy, wz;
-        lin_axis(x, cx, x0, wx);
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    // rows start 16-byte aligned (NX % 4 == 0): output pairs are 8-byte
+    // aligned when the model's first column is even
+    const bool pairs = (G.nb % 2) == 0;
+    for (long long row = warp; row < (long long)G.ny * G.nz; row += nwarps) {
+        const int y = (int)(row % G.ny), z = (int)(row / G.ny);
+        int y0, z0;
+        float wy, wz;
         lin_axis(y, cy, y0, wy);
         lin_axis(z, cz, z0, wz);
-        const int x1 = wx > 0.f ? x0 + 1 : x0, y1 = wy > 0.f ? y0 + 1 : y0,
-                  z1 = wz > 0.f ? z0 + 1 : z0;
+        const int y1 = wy > 0.f ? y0 + 1 : y0, z1 = wz > 0.f ? z0 + 1 : z0;
         const float* r00 = coarse + ((long long)z0 * cy + y0) * cx;
         const float* r01 = coarse + ((long long)z0 * cy + y1) * cx;
         const float* r10 = coarse + ((long long)z1 * cy + y0) * cx;
         const float* r11 = coarse + ((long long)z1 * cy + y1) * cx;
-        const float a00 = (1.f - wx) * __ldg(r00 + x0) + wx * __ldg(r00 + x1);
-        const float a01 = (1.f - wx) * __ldg(r01 + x0) + wx * __ldg(r01 + x1);
-        const float a10 = (1.f - wx) * __ldg(r10 + x0) + wx * __ldg(r10 + x1);
-        const float a11 = (1.f - wx) * __ldg(r11 + x0) + wx * __ldg(r11 + x1);
-        const float b0 = (1.f - wy) * a00 + wy * a01;
-        const float b1 = (1.f - wy) * a10 + wy * a11;
-        slab[((long long)z * G.ny + y) * G.NX + G.nb + x] = (1.f - wz) * b0 + wz * b1;
+        float* out = slab + row * G.NX + G.nb;
+        auto kept = [&](int k) {  // kept column k interpolated along y, then z
+            const float a0 = (1.f - wy) * __ldg(r00 + k) + wy * __ldg(r01 + k);
+            const float a1 = (1.f - wy) * __ldg(r10 + k) + wy * __ldg(r11 + k);
+            return (1.f - wz) * a0 + wz * a1;
+        };
+        // four groups of 32 kept columns at a time: their loads are in flight together
+        constexpr int U = 4;
+        for (int base = 0; base < cx; base += 32 * U) {
+            float bk[U + 1];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int k = base + 32 * u + lane;
+                bk[u] = k < cx ? kept(k) : 0.f;
+            }
+            const int kl = base + 32 * U;  // the column after the last group, for lane 31
+            bk[U] = (lane == 31 && kl < cx) ? kept(kl) : 0.f;
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int k = base + 32 * u + lane;
+                // the next kept column: lane + 1's, or for lane 31 the next
+                // group's first (lane 0), or the extra column after the last group
+                const float right = __shfl_down_sync(0xffffffffu, bk[u], 1);
+                const float head = __shfl_sync(0xffffffffu, u + 1 < U ? bk[u + 1] : 0.f, 0);
+                const float bn = lane < 31 ? right : (u + 1 < U ? head : bk[U]);
+                if (k < cx) {
+                    const float odd = k + 1 < cx ? 0.5f * bk[u] + 0.5f * bn : bk[u];
+                    if (pairs && 2 * k + 1 < G.nx) {  // whole lines per warp
+                        __stcs(reinterpret_cast<float2*>(out + 2 * k), make_float2(bk[u], odd));
+                    } else {
+                        __stcs(out + 2 * k, bk[u]);
+                        if (2 * k + 1 < G.nx) __stcs(out + 2 * k + 1, odd);
+                    }
+                }
+            }
+        }
     }
 }
 
@@ -477,16 +510,22 @@ cudaError_t launch_finite_scan(const float* f, long long n, int* status, cudaStr
     return cudaGetLastError();
 }
 
+// rows of a row-walking kernel: 16 resident blocks per SM on 152 SMs at most
+static int row_blocks(long long rows) { return (int)(rows < 152 * 16 ? rows : 152 * 16); }
+
 cudaError_t launch_decimate(const Geometry& G, const float* u, float* coarse, cudaStream_t s) {
     const int cx = (G.nx + 1) / 2, cy = (G.ny + 1) / 2, cz = (G.nz + 1) / 2;
-    k_decimate<<<grid_for((long long)cx * cy * cz, 256), 256, 0, s>>>(G, u, coarse, cx, cy, cz);
+    const int tb = cx > 128 ? 256 : 128;
+    k_decimate<<<row_blocks((long long)cy * cz), tb, 0, s>>>(G, u, coarse, cx, cy, cz);
     return cudaGetLastError();
 }
 
 cudaError_t launch_upsample(const Geometry& G, const float* coarse, float* slab, cudaStream_t s) {
     const int cx = (G.nx + 1) / 2, cy = (G.ny + 1) / 2, cz = (G.nz + 1) / 2;
-    k_upsample<<<grid_for((long long)G.nx * G.ny * G.nz, 256), 256, 0, s>>>(G, coarse, cx, cy,
-                                                                            cz, slab);
+    // a warp per row: 256-thread blocks, eight resident per SM
+    const long long rows = (long long)G.ny * G.nz;
+    const int blocks = (int)std::min<long long>((rows + 7) / 8, 152 * 8);
+    k_upsample<<<blocks, 256, 0, s>>>(G, coarse, cx, cy, cz, slab);
     return cudaGetLastError();
 }
 
