@@ -89,12 +89,14 @@ __device__ __forceinline__ Vec<V> vld_cg(const float* p) {  // global, coherent 
     }
     return r;
 }
+// global store, streaming (evict first): every field a step writes is read
+// again only in a later step, after the rest of the wave has gone through L2
 template <int V>
 __device__ __forceinline__ void vst(float* p, const Vec<V>& a) {
     if constexpr (V == 4)
-        *reinterpret_cast<float4*>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
+        __stcs(reinterpret_cast<float4*>(p), make_float4(a.v[0], a.v[1], a.v[2], a.v[3]));
     else
-        *reinterpret_cast<float2*>(p) = make_float2(a.v[0], a.v[1]);
+        __stcs(reinterpret_cast<float2*>(p), make_float2(a.v[0], a.v[1]));
 }
 
 __device__ __forceinline__ uint32_t s_u32(const void* p) {
@@ -104,21 +106,25 @@ __device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(b)), "r"(bytes)
                  : "memory");
 }
+__device__ __forceinline__ bool bar_poll(uint32_t a, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return done != 0;
+}
 // bounded wait; false if it ran out (then the launch's abort flag is raised)
 // or if another block already aborted
 __device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, BatchCtrl* ctrl) {
     const uint32_t a = s_u32(b);
+    if (bar_poll(a, parity)) return true;  // the common case: the plane is in
     const unsigned long long t0 = wait_now();
     for (long long i = 0; i < kPlaneWaitLimit; i++) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.b32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
+        if (bar_poll(a, parity)) return true;
         if ((i & 1023) == 1023 && *reinterpret_cast<volatile int*>(&ctrl->abort)) return false;
         if (wait_expired(i, t0)) break;
     }
@@ -131,17 +137,8 @@ __device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, BatchCtrl
 __device__ __forceinline__ void bar_drain(uint64_t* b, uint32_t parity) {
     const uint32_t a = s_u32(b);
     const unsigned long long t0 = wait_now();
-    for (long long i = 0; i < kPlaneWaitLimit; i++) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.b32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done || wait_expired(i, t0)) return;
-    }
+    for (long long i = 0; i < kPlaneWaitLimit; i++)
+        if (bar_poll(a, parity) || wait_expired(i, t0)) return;
 }
 __device__ __forceinline__ void bar_arrive(uint64_t* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_u32(b)) : "memory");
@@ -475,7 +472,11 @@ __global__ void __launch_bounds__(16 * BY, BT<R, BY>::MINB)
     __shared__ __align__(8) uint64_t ubar[B::NS];
     __shared__ __align__(8) uint64_t abar[B::NS];
     __shared__ long long s_item;
-    __shared__ int s_go;
+    __shared__ int s_go, s_shot_i;
+    // the item's shot, copied once per item: its fields are read again in
+    // every plane, and shared-memory reads of them are cheaper than global
+    // ones that each store of the plane before may have overwritten
+    __shared__ BatchShot s_shot;
     const BatchArgs& A = T.a;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     if (tid == 0) {
@@ -495,18 +496,22 @@ __global__ void __launch_bounds__(16 * BY, BT<R, BY>::MINB)
         if (item >= total) break;
         const int t = (int)(item / A.items_per_phase);
         const long long r = item % A.items_per_phase;
-        int s = 0;
-        while (s + 1 < A.nshots && A.shots[s + 1].item_base <= r) s++;
-        const BatchShot& S = A.shots[s];
-        const int tile = (int)(r - S.item_base);
         if (tid == 0) {
-            unsigned int target = (unsigned int)t * (unsigned int)S.ntiles;
+            int s = 0;
+            while (s + 1 < A.nshots && A.shots[s + 1].item_base <= r) s++;
+            s_shot = A.shots[s];
+            s_shot_i = s;
+            const int tile = (int)(r - A.shots[s].item_base);
+            unsigned int target = (unsigned int)t * (unsigned int)A.shots[s].ntiles;
             if (s == A.poison_shot && t == 0 && tile == 0) target = 0xFFFFFFFFu;  // failure test
             s_go = wait_counter(A.ctrl, &A.ctrl->done[s], target, A.timeout_cycles, A.status) ? 1
                                                                                          : 0;
         }
         __syncthreads();
         if (!s_go) break;
+        const int s = s_shot_i;
+        const BatchShot& S = s_shot;
+        const int tile = (int)(r - S.item_base);
         const bool ok = item_tma<R, BY>(T, S, A.phases[t], tile, s, uring, aring, ubar, abar, rp);
         __threadfence();
         __syncthreads();
