@@ -205,14 +205,16 @@ __device__ __forceinline__ bool bar_poll(uint32_t a, uint32_t parity) {
     return done != 0;
 }
 // bounded wait (poll count and elapsed time); false if it ran out (then the
-// block's abort flag is raised) or if the block already aborted
+// block's abort flag is raised) or if the block aborted while it waited. The
+// caller reads the abort flag once per plane, before its waits: a completed
+// phase answers the first poll without a shared-memory read of the flag
 __device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, int* abort_flag) {
-    if (*reinterpret_cast<volatile int*>(abort_flag)) return false;
     const uint32_t a = s_u32(b);
     if (bar_poll(a, parity)) return true;  // the common case: the plane is in
     const unsigned long long t0 = wait_now();
     for (long long i = 0; i < kTmaWaitLimit; i++) {
         if (bar_poll(a, parity)) return true;
+        if (*reinterpret_cast<volatile int*>(abort_flag)) return false;
         if (wait_expired(i, t0)) break;
     }
     *reinterpret_cast<volatile int*>(abort_flag) = 1;
@@ -368,13 +370,13 @@ __global__ void __launch_bounds__(16 * BY, (tma_min_blocks<R, MODE, BY>()))
             if (pu <= last_u) issue_u(pu);
             if (z + C::P < ze) issue_a(z + C::P);
         }
-        bool ok = true;
+        bool ok = !*reinterpret_cast<volatile int*>(&abort_flag);  // once per plane
         if constexpr (!C::SPLIT) {
-            ok = bar_wait(&ubar[shd], (uint32_t)phd, &abort_flag);
+            ok = ok && bar_wait(&ubar[shd], (uint32_t)phd, &abort_flag);
             q[2 * R + t] = vlds<V>(uring + shd * C::UPLANE + own_off);
         }
-        ok = bar_wait(&ubar[sc], (uint32_t)pc, &abort_flag) && ok;
-        ok = bar_wait(&abar[sa], (uint32_t)pa, &abort_flag) && ok;
+        ok = ok && bar_wait(&ubar[sc], (uint32_t)pc, &abort_flag);
+        ok = ok && bar_wait(&abar[sa], (uint32_t)pa, &abort_flag);
         const float* S = uring + sc * C::UPLANE;
         const float* aux = aring + sa * C::NAH * C::APLANE;
         if constexpr (C::SPLIT) q[2 * R + t] = vlds<V>(aux + NA * C::APLANE + aux_off);
