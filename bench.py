@@ -61,7 +61,7 @@ def parse():
                     help="skip the learned-compression leg (384^3, 3000 steps)")
     ap.add_argument("--learned-train-steps", type=int, default=8000)
     ap.add_argument("--learned-models", type=int, default=64)
-    ap.add_argument("--learned-window", type=int, default=200,
+    ap.add_argument("--learned-window", type=int, default=120,
                     help="exact window: the first steps whose snapshots are recomputed from the "
                          "zero state instead of coded (checkpoint-recompute fallback)")
     ap.add_argument("--zchunk", type=int, default=0,
