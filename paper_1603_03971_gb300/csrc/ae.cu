@@ -725,17 +725,45 @@ struct OpD1w {  // dW3[o][k][i] += sum_j ga3[2j + q][o] lat[j + t][i], class q =
 // ============================================================================
 // CUDA-core kernels
 // ============================================================================
-// sum of squares of a strided volume: a warp per row of x (float4 loads when
-// rows are 16-byte aligned), 8 rows per block, float partials per thread (four
+// sum of squares of a strided volume: float partials per thread (four
 // accumulators over at most a few hundred values), a block reduction in
-// double, one atomic per block
+// double, one atomic per block. A contiguous 16-byte aligned volume is read
+// as one flat float4 array, four loads in flight per thread; otherwise a
+// warp per row of x (float4 loads when rows are 16-byte aligned), 8 rows per
+// block
 __global__ void __launch_bounds__(256) k_sumsq(Vol in, double* acc) {
     const long long rows = (long long)in.ny * in.nz;
     const int lane = threadIdx.x, nx4 = in.nx >> 2;
     const bool vec = ((reinterpret_cast<uintptr_t>(in.p) & 15) == 0) && (in.sy % 4 == 0) &&
                      (in.sz % 4 == 0) && (in.nx % 4 == 0);
+    const bool flat = vec && in.sy == in.nx && in.sz == (long long)in.nx * in.ny;
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    for (long long r = (long long)blockIdx.x * blockDim.y + threadIdx.y; r < rows;
+    if (flat) {
+        const float4* p4 = reinterpret_cast<const float4*>(in.p);
+        const long long n4 = rows * nx4;
+        const long long step = (long long)gridDim.x * blockDim.x * blockDim.y;
+        long long i = (long long)blockIdx.x * blockDim.x * blockDim.y + threadIdx.y * 32 + lane;
+        for (; i + 3 * step < n4; i += 4 * step) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) v[u] = __ldg(p4 + i + u * step);
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                s0 = fmaf(v[u].x, v[u].x, s0);
+                s1 = fmaf(v[u].y, v[u].y, s1);
+                s2 = fmaf(v[u].z, v[u].z, s2);
+                s3 = fmaf(v[u].w, v[u].w, s3);
+            }
+        }
+        for (; i < n4; i += step) {
+            const float4 v = __ldg(p4 + i);
+            s0 = fmaf(v.x, v.x, s0);
+            s1 = fmaf(v.y, v.y, s1);
+            s2 = fmaf(v.z, v.z, s2);
+            s3 = fmaf(v.w, v.w, s3);
+        }
+    }
+    for (long long r = (long long)blockIdx.x * blockDim.y + threadIdx.y; r < rows && !flat;
          r += (long long)gridDim.x * blockDim.y) {
         const int y = (int)(r % in.ny), z = (int)(r / in.ny);
         const float* row = in.p + (long long)z * in.sz + (long long)y * in.sy;

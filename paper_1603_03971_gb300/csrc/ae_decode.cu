@@ -61,6 +61,7 @@ constexpr int kSmem = 128 + kW3Bytes + kSlots * kPlaneBytes + 128 + 1024 + 2 * 4
 constexpr int kTmemCols = 512;
 constexpr int kThreads = 288;
 constexpr long long kLimit = 1LL << 24;
+constexpr uint32_t kSuspendNs = 20000;  // longest sleep of one poll (woken by the phase)
 
 struct Sched {
     int ncx, ncy, nzc, zc, nitems;
@@ -100,17 +101,10 @@ __device__ __forceinline__ void bar_arrive(uint64_t* b) {
 // bounded wait; gives up early once another thread has raised the abort flag
 __device__ __forceinline__ bool wait_bar(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
     const uint32_t a = tc::smem_u32(b);
+    if (mbar_try_wait_sleep(a, parity, kSuspendNs)) return true;
     const unsigned long long t0 = wait_now();
     for (long long i = 0; i < kLimit; i++) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.b32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
+        if (mbar_try_wait_sleep(a, parity, kSuspendNs)) return true;
         if (abort_flag && *abort_flag) return false;
         if (wait_expired(i, t0)) break;
     }

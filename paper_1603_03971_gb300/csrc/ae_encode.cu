@@ -7,39 +7,52 @@
 // planes z. Latent plane z reads h1 planes 2z - 1, 2z, 2z + 1; each h1 plane
 // of the column is a 17 x 33 tile (one h1 voxel of halo on the low side)
 // computed from two snapshot planes, which TMA copies (40 x 66 floats, zeros
-// outside the volume) into a four-slot ring.
+// outside the volume) into a three-slot ring; a loader thread (warp 21)
+// issues each copy as soon as its slot is free.
 //
-// E1 runs on the tensor cores as well: for each h1 plane, the warpgroup that
-// owns it (warpgroup 1 even planes, warpgroup 2 odd ones; three snapshot
-// slots, so that a warpgroup's next copy overlaps its current plane) writes
+// E1 runs on the tensor cores as well. Two E1 roles of 256 threads (warps
+// 1-8: even h1 planes, warps 9-16: odd ones) each write, for their plane,
 // the bf16(s / rms) values of every h1 voxel's 2 x 2 x 2 patch as one row of
-// a 648-row A tile, the issuing thread runs 5 tcgen05.mma (M = 128 voxels,
+// a 648-row A tile (rows in h1 slot order, below: row 17 iy + slot, so that
+// one float4 of the snapshot row serves two voxels and the epilogue's
+// stores are contiguous); once all 256 rows are in (mbarrier of 256
+// arrivals) the role's first thread issues 5 tcgen05.mma (M = 128 voxels,
 // N = 32, K = 16: the 8 patch values, then 8 columns multiplied by the zero
-// half of W1) into that warpgroup's 160 TMEM columns, and the warpgroup adds
-// b1, applies LeakyReLU, rounds to bf16 and stores h1 into a three-slot ring
-// laid out as E2's A operand in the canonical K-major no-swizzle layout:
-// four 8-channel core-matrix columns (leading byte offset 8976 B) of
-// [33][17] 16-byte rows, with the x positions split by parity (9 even, then
-// 8 odd) so that every tap of the stride-2 convolution reads 8 consecutive
-// rows: tap (kz, ky, kx) of latent row (ly, lx) is h1 row 2 ly + ky, slot lx
-// (kx = 0), 9 + lx (kx = 1) or lx + 1 (kx = 2); 8-row groups (one per ly)
-// are 544 B apart. The products, sums and rounding points are those of the
-// GEMM-engine encoder, so the latents are the same.
+// half of W1) into the role's 160 TMEM columns. Each warp of a role reads
+// its 32 TMEM lanes of 16 of the 32 channels (the role's first warpgroup
+// channels 0-15, the second 16-31), one M tile loading while the one before
+// it is processed, adds b1, applies LeakyReLU (packed f32x2 arithmetic),
+// rounds to bf16 and stores h1 into a three-slot ring laid out as E2's A
+// operand in the canonical K-major no-swizzle layout: four 8-channel
+// core-matrix columns (leading byte offset 8976 B) of [33][17] 16-byte
+// rows, with the x positions split by parity (9 even, then 8 odd) so that
+// every tap of the stride-2 convolution reads 8 consecutive rows: tap (kz,
+// ky, kx) of latent row (ly, lx) is h1 row 2 ly + ky, slot lx (kx = 0), 9 +
+// lx (kx = 1) or lx + 1 (kx = 2); 8-row groups (one per ly) are 544 B apart.
+// The products, sums and rounding points are those of the GEMM-engine
+// encoder, so the latents are the same.
 //
 // E2 runs on the tensor cores, one h1 plane at a time: as soon as plane p is
-// complete, one thread issues its 9 taps x 2 tcgen05.mma (M = 128 latent
-// voxels, N = 16, K = 16 channels) into the accumulator of every latent plane
-// that reads it (plane 2m: kz = 2 of latent m - 1, then kz = 0 of latent m;
-// plane 2m + 1: kz = 1 of latent m), so each latent sums its 27 taps in the
-// order of the GEMM-engine encoder and each h1 slot is freed after one use.
-// Two 16-column accumulators alternate between latent planes; warpgroup 3
-// adds b2, rounds to bf16 and stores the latent rows. The issuing thread runs
-// an event loop of non-blocking mbarrier tests (snapshot slot free -> next
-// copy; A tile built -> E1 MMAs; h1 plane complete and accumulator free ->
-// its E2 MMAs). mbarriers: snapshot full (TMA bytes) / free (128 arrivals),
-// A tile full (128 arrivals) / E1 done (commit), h1 full (128 arrivals) /
-// free (commit), accumulator full (commit) / free (128 arrivals). Every wait
-// is bounded and shares an abort flag.
+// complete, the E2 issuer (warp 0) issues its 9 taps x 2 K halves of
+// tcgen05.mma (M = 128 latent voxels, K = 16 channels) into the accumulator
+// of every latent plane that reads it (plane 2m: kz = 2 of latent m - 1 and
+// kz = 0 of latent m, as N = 32 MMAs into both accumulators at once after a
+// first tap of two N = 16 MMAs; plane 2m + 1: kz = 1 of latent m, N = 16),
+// so each latent sums its 27 taps in the order of the GEMM-engine encoder
+// and each h1 slot is freed after one use. Two 16-column accumulators
+// (TMEM columns 0-15 and 16-31) alternate between latent planes; warps
+// 17-20 add b2, round to bf16 and store the latent rows. mbarriers:
+// snapshot full (TMA bytes) / free (256 arrivals), A tile full (256
+// arrivals) / E1 done (commit), h1 full (256 arrivals) / free (commit),
+// accumulator full (commit) / free (128 arrivals). Every wait is bounded,
+// shares an abort flag and sleeps in the mbarrier poll instead of spinning.
+//
+// Measured with per-stage clock stamps at 384^3 (one h1 plane every ~2700
+// cycles per CTA): a single issuing thread for E1 and E2, snapshot copies
+// and E2 MMAs in one event loop, and one warpgroup per E1 role made the E1
+// MMAs wait ~1900 cycles per plane behind the E2 issue and the epilogue of
+// one plane take ~4000 cycles; pairing the kz = 2 and kz = 0 MMAs cut the
+// E2 issue from ~2060 to ~1560 cycles per plane.
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -48,6 +61,7 @@
 #include <algorithm>
 
 #include "ae_internal.h"
+#include "packed_f32x2.cuh"
 #include "tc_gemm.cuh"
 #include "tma_encode.h"
 #include "wait_clock.cuh"
@@ -63,21 +77,28 @@ constexpr int NVOX = HX * HY;           // 561
 constexpr int kRowBytes = HX * 16;      // one h1 row of one 8-channel column: 272 B
 constexpr int kKcBytes = HY * kRowBytes;                 // 8976 B
 constexpr int kH1Bytes = 35968;                          // 4 columns (35904 B), 128-aligned
+static_assert(32 * kRowBytes + 16 * 16 + 2 * kKcBytes < 65536, "h1 row offsets fit 16 bits");
 constexpr int SX = 40, SYR = 2 * HY;                     // snapshot box: 40 x 66 x 2
 constexpr int kSnapBytes = SX * SYR * 2 * 4;             // 21120
-constexpr int kW2Bytes = 54 * 512;                       // 27 taps x 2 halves of 16 x 16
+// E2 B operands, per (tap t9 of a kz, K half): region C holds kz = 2 and 0
+// as a 48-row block [kz 2 | kz 0 | kz 2] (1536 B), so that 16-row operands of
+// either kz and 32-row operands of both, in either order, are contiguous;
+// region K1 holds kz = 1 (16 rows, 512 B)
+constexpr int kW2CBlock = 1536, kW2CBytes = 18 * kW2CBlock;
+constexpr int kW2Bytes = kW2CBytes + 18 * 512;
 constexpr int kSS = 3, kSH = 3;
-constexpr int kLook = 3;  // snapshot loads ahead of the next h1 plane to multiply
-constexpr long long kIdleLimit = 1LL << 26;  // producer loop turns without progress
 constexpr int kW1Bytes = 1024;      // W1 as a 32 x 16 operand (k 8..15 zero)
 constexpr int kARows = 648;         // E1 A tile: 5 M tiles of 128 rows + 8 rows read as K half 2
 constexpr int kATileBytes = kARows * 16;                 // 10368
 constexpr int kE1Col = 32;          // E1 accumulators: 2 x (5 x 32) TMEM columns from here
 constexpr int kSmem = 128 + kW2Bytes + kW1Bytes + kSS * kSnapBytes + kSH * kH1Bytes +
                       2 * kATileBytes;
-constexpr int kThreads = 13 * 32;
+static_assert(kSmem + 1024 <= 227 * 1024, "shared memory of one CTA");
+constexpr int kE1Threads = 256;   // threads of one E1 role (two warpgroups)
+constexpr int kThreads = 22 * 32;
 constexpr int kTmemCols = 512;
 constexpr long long kLimit = 1LL << 24;
+constexpr uint32_t kSuspendNs = 20000;  // longest sleep of one poll (woken by the phase)
 
 struct Sched {
     int ncx, ncy, zc, nitems;
@@ -98,7 +119,7 @@ __device__ __forceinline__ void item_coords(const Sched& S, int lnz, int item, i
     nz = min(S.zc, lnz - z0);
 }
 
-__device__ __forceinline__ float lrelu(float a) { return a > 0.f ? a : kSlope * a; }
+static_assert(kSlope > 0.f && kSlope < 1.f, "LeakyReLU as a maximum needs 0 < slope < 1");
 
 __device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(b)),
@@ -110,17 +131,10 @@ __device__ __forceinline__ void bar_arrive(uint64_t* b) {
 }
 __device__ __forceinline__ bool wait_bar(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
     const uint32_t a = tc::smem_u32(b);
+    if (mbar_try_wait_sleep(a, parity, kSuspendNs)) return true;
     const unsigned long long t0 = wait_now();
     for (long long i = 0; i < kLimit; i++) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.b32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
+        if (mbar_try_wait_sleep(a, parity, kSuspendNs)) return true;
         if (abort_flag && *abort_flag) return false;
         if (wait_expired(i, t0)) break;
     }
@@ -136,41 +150,82 @@ __device__ __forceinline__ void tma_snap(float* dst, const CUtensorMap* map, int
         : "memory");
 }
 
-__device__ __forceinline__ bool test_bar(uint64_t* b, uint32_t parity) {
-    uint32_t done;
+
+// 16 columns at a TMEM address (one M tile) of this warp's lanes into r,
+// without waiting: the registers must not be read before tmem_wait_regs(r)
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t a0, uint32_t* r) {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.b32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(tc::smem_u32(b)), "r"(parity)
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(a0)
         : "memory");
-    return done != 0;
+}
+// wait for this thread's TMEM loads; the registers are operands, so no read
+// of them can be scheduled before the wait
+__device__ __forceinline__ void tmem_wait_regs(uint32_t* r) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
 }
 
 // byte offset of (row o, k) in a 16 x 16 K-major operand (LBO 128, SBO 256)
 __device__ __forceinline__ int b_off(int o, int k) {
     return (o >> 3) * 256 + (k >> 3) * 128 + (o & 7) * 16 + (k & 7) * 2;
 }
-// shared-memory row slot of h1 tile column ix (even positions first)
-__device__ __forceinline__ int x_slot(int ix) { return (ix & 1) ? 9 + (ix >> 1) : (ix >> 1); }
 
-// the 9 taps of one kz (K = 32 channels each, two K = 16 MMAs) from the h1
-// plane described by dA into the accumulator at column acc, in the tap order
-// of the GEMM-engine encoder; the descriptors' start-address field is
-// address >> 4 and no operand crosses 256 KB, so offsets add to the field
-__device__ __forceinline__ void issue_taps(uint32_t acc, uint64_t dA, uint64_t dB, int kz,
+// byte offset of the h1 rows that tap t9 (ky, kx) of a latent row reads
+__device__ __forceinline__ uint32_t tap_off(int t9) {
+    const int ky = t9 / 3, kx = t9 % 3;
+    const int slot0 = kx == 0 ? 0 : (kx == 1 ? 9 : 1);
+    return (uint32_t)(ky * kRowBytes + slot0 * 16);
+}
+
+// the 9 taps of one kz (K = 32 channels each, two K = 16 MMAs, N = 16) from
+// the h1 plane described by dA into the accumulator at column acc, in the tap
+// order of the GEMM-engine encoder; dB addresses the kz's operand of tap 0,
+// K half 0, and (t9, half) operands are `stride` bytes apart. The
+// descriptors' start-address field is address >> 4 and no operand crosses
+// 256 KB, so offsets add to the field
+__device__ __forceinline__ void issue_taps(uint32_t acc, uint64_t dA, uint64_t dB, int stride,
                                            bool first, uint32_t idesc) {
 #pragma unroll
     for (int t9 = 0; t9 < 9; t9++) {
-        const int ky = t9 / 3, kx = t9 % 3, tap = kz * 9 + t9;
-        const int slot0 = kx == 0 ? 0 : (kx == 1 ? 9 : 1);
-        const uint32_t off = (uint32_t)(ky * kRowBytes + slot0 * 16);
+        const uint32_t off = tap_off(t9);
 #pragma unroll
         for (int hh = 0; hh < 2; hh++)
             tc::mma_bf16(acc, dA + (uint64_t)((off + hh * 2 * kKcBytes) >> 4),
-                         dB + (uint64_t)((tap * 2 + hh) * 32), idesc,
+                         dB + (uint64_t)(((t9 * 2 + hh) * stride) >> 4), idesc,
                          (first && t9 == 0 && hh == 0) ? 0u : 1u);
+    }
+}
+
+// an h1 plane that closes one latent plane (kz = 2, accumulating) and opens
+// the next (kz = 0): the first tap as two N = 16 MMAs (the opening
+// accumulator is overwritten), the other 17 as N = 32 MMAs into both
+// accumulators at once (columns 0-31; B rows 0-15 go to columns 0-15).
+// kz0_low: the opening plane's accumulator is columns 0-15
+__device__ __forceinline__ void issue_pair(uint32_t tmem, uint64_t dA, uint64_t dC, bool kz0_low,
+                                           uint32_t idesc16, uint32_t idesc32) {
+    const uint32_t acc_open = tmem + (kz0_low ? 0 : 16), acc_close = tmem + (kz0_low ? 16 : 0);
+    const uint64_t dB32 = dC + (uint64_t)((kz0_low ? 512 : 0) >> 4);
+    const uint32_t off0 = tap_off(0);
+    tc::mma_bf16(acc_close, dA + (uint64_t)(off0 >> 4), dC, idesc16, 1u);
+    tc::mma_bf16(acc_open, dA + (uint64_t)(off0 >> 4), dC + (uint64_t)(512 >> 4), idesc16, 0u);
+#pragma unroll
+    for (int t9 = 0; t9 < 9; t9++) {
+        const uint32_t off = tap_off(t9);
+#pragma unroll
+        for (int hh = 0; hh < 2; hh++) {
+            if (t9 == 0 && hh == 0) continue;
+            tc::mma_bf16(tmem, dA + (uint64_t)((off + hh * 2 * kKcBytes) >> 4),
+                         dB32 + (uint64_t)(((t9 * 2 + hh) * kW2CBlock) >> 4), idesc32, 1u);
+        }
     }
 }
 
@@ -223,16 +278,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
         for (int s = 0; s < kSS; s++) {
             tc::mbar_init(&snap_full[s], 1);
-            tc::mbar_init(&snap_free[s], 128);
+            tc::mbar_init(&snap_free[s], kE1Threads);
         }
         for (int s = 0; s < kSH; s++) {
-            tc::mbar_init(&h1_full[s], 128);
+            tc::mbar_init(&h1_full[s], kE1Threads);
             tc::mbar_init(&h1_free[s], 1);
         }
         for (int b = 0; b < 2; b++) {
             tc::mbar_init(&acc_full[b], 1);
             tc::mbar_init(&acc_free[b], 128);
-            tc::mbar_init(&e1a_full[b], 128);
+            tc::mbar_init(&e1a_full[b], kE1Threads);
             tc::mbar_init(&e1_done[b], 1);
         }
         tc::mbar_init(&fin, 1);
@@ -240,13 +295,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) tc::tmem_alloc(&tmem_slot, kTmemCols);
-    // E2 B operands: (tap, half) -> W2[o][tap][16 half + i], 16 x 16 K-major
+    // E2 B operands: (tap, half) -> W2[o][tap][16 half + i], 16-row K-major
+    // blocks in region C (kz 0 and 2) or K1 (kz 1)
     for (int idx = tid; idx < 54 * 16 * 2; idx += kThreads) {
         const int j = idx & 1, o = (idx >> 1) & 15, t = idx >> 5, tap = t >> 1, hh = t & 1;
         float w[8];
 #pragma unroll
         for (int e = 0; e < 8; e++) w[e] = A.P[kOW2 + o * 864 + tap * 32 + 16 * hh + 8 * j + e];
-        *reinterpret_cast<uint4*>(w2 + t * 512 + b_off(o, 8 * j)) = tc::pack8(w);
+        const uint4 v = tc::pack8(w);
+        const int kz = tap / 9, blk = (tap % 9) * 2 + hh, bo = b_off(o, 8 * j);
+        if (kz == 1) {
+            *reinterpret_cast<uint4*>(w2 + kW2CBytes + blk * 512 + bo) = v;
+        } else if (kz == 0) {
+            *reinterpret_cast<uint4*>(w2 + blk * kW2CBlock + 512 + bo) = v;
+        } else {
+            *reinterpret_cast<uint4*>(w2 + blk * kW2CBlock + bo) = v;
+            *reinterpret_cast<uint4*>(w2 + blk * kW2CBlock + 1024 + bo) = v;
+        }
     }
     // E1 B operand: W1[o][dz][dy][dx] as k = 0..7 of row o; k = 8..15 zero
     if (tid < 64) {
@@ -270,116 +335,81 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- producer: snapshot loads and E2 MMAs ----------------
-            // An event loop of non-blocking barrier tests: a snapshot load is
-            // issued when its slot is free (at most kLook planes ahead of the MMAs),
-            // and the MMAs of h1 plane mp when that plane is complete. Plane 2m of
-            // an item closes latent plane m - 1 (kz = 2) and opens latent plane m
-            // (kz = 0); plane 2m + 1 is kz = 1 of latent plane m.
-            constexpr uint32_t idesc = tc::idesc_bf16(128, 16);
+            // ---------------- E2 issuer ----------------
+            // the MMAs of h1 plane mp once that plane is complete (and, for a
+            // plane that opens a latent plane, once its accumulator is free).
+            // Plane 2m of an item closes latent plane m - 1 (kz = 2) and opens
+            // latent plane m (kz = 0); plane 2m + 1 is kz = 1 of latent plane m.
+            constexpr uint32_t idesc = tc::idesc_bf16(128, 16), idesc32 = tc::idesc_bf16(128, 32);
             const uint32_t h1_a = tc::smem_u32(h1);
             const uint64_t dB0 = tc::sdesc(tc::smem_u32(w2), 128, 256);
-            int np = 0;  // h1 planes of this CTA
-            for (int item = blockIdx.x; item < S.nitems; item += gridDim.x) {
-                int cx, cy, z0, nz;
-                item_coords(S, lnz, item, cx, cy, z0, nz);
-                np += 2 * nz + 1;
-            }
-            PlaneCursor L, M;
-            L.start(S, lnz);
+            PlaneCursor M;
             M.start(S, lnz);
-            int l_seq = 0, mp = 0, obase = 0;
-            int e1_next[2] = {0, 1};  // next h1 plane of each E1 warpgroup
-            constexpr uint32_t idesc1 = tc::idesc_bf16(128, 32);
-            const uint64_t dW1 = tc::sdesc(tc::smem_u32(w1), 128, 256);
-            long long idle = 0;
+            int obase = 0;
             bool ok = true;
-            while (mp < np && ok) {
-                bool prog = false;
-#pragma unroll
-                for (int g = 0; g < 2; g++) {
-                    const int j = e1_next[g];
-                    if (j < np && test_bar(&e1a_full[g], (uint32_t)((j >> 1) & 1))) {
-                        // E1 of plane j: 5 M tiles of 128 voxels, K = 16 (8 inputs + 8 zeros)
-                        tc::tc_fence_after();
-                        const uint32_t a0 = tc::smem_u32(atile + g * kATileBytes);
-#pragma unroll
-                        for (int t = 0; t < 5; t++)
-                            tc::mma_bf16(tmem + kE1Col + g * 160 + t * 32,
-                                         tc::sdesc(a0 + t * 2048, 128, 128), dW1, idesc1, 0u);
-                        tc::mma_commit(&e1_done[g]);
-                        e1_next[g] = j + 2;
-                        prog = true;
-                    }
+            for (int mp = 0; M.valid(S); mp++) {
+                ok = wait_bar(&h1_full[mp % kSH], (uint32_t)((mp / kSH) & 1), abrt);
+                if (!ok) break;
+                const int k = M.k, n = M.n, m = k >> 1;
+                const bool opens = !(k & 1) && m < n;
+                const int og = obase + m;  // global latent plane opened (k even) or continued
+                if (opens && og >= 2)
+                    ok = wait_bar(&acc_free[og & 1], (uint32_t)(((og >> 1) - 1) & 1), abrt);
+                if (!ok) break;
+                tc::tc_fence_after();
+                uint64_t dB;
+                asm volatile("mov.b64 %0, %1;" : "=l"(dB) : "l"(dB0));
+                const uint64_t dA =
+                    tc::sdesc(h1_a + (mp % kSH) * kH1Bytes, kKcBytes, 2 * kRowBytes);
+                // dB: region C (kz 2 at +0, kz 0 at +512); region K1 at +kW2CBytes
+                if (k & 1) {
+                    issue_taps(tmem + (og & 1) * 16, dA, dB + (uint64_t)(kW2CBytes >> 4), 512,
+                               false, idesc);
+                } else if (m >= 1 && opens) {
+                    issue_pair(tmem, dA, dB, (og & 1) == 0, idesc, idesc32);
+                    tc::mma_commit(&acc_full[(og - 1) & 1]);
+                } else if (m >= 1) {
+                    issue_taps(tmem + ((og - 1) & 1) * 16, dA, dB, kW2CBlock, false, idesc);
+                    tc::mma_commit(&acc_full[(og - 1) & 1]);
+                } else if (opens) {
+                    issue_taps(tmem + (og & 1) * 16, dA, dB + (uint64_t)(512 >> 4), kW2CBlock,
+                               true, idesc);
                 }
-                if (l_seq < np && l_seq <= mp + kLook) {
-                    const int slot = l_seq % kSS;
-                    if (l_seq < kSS || test_bar(&snap_free[slot], (uint32_t)((l_seq / kSS - 1) & 1))) {
-                        int lcx, lcy, lz0, lnzi;
-                        item_coords(S, lnz, L.item, lcx, lcy, lz0, lnzi);
-                        bar_expect(&snap_full[slot], kSnapBytes);
-                        tma_snap(snap + slot * (kSnapBytes / 4), &map, 32 * lcx - 4, 64 * lcy - 2,
-                                 2 * (2 * lz0 - 1 + L.k), &snap_full[slot]);
-                        l_seq++;
-                        L.next(S, lnz);
-                        prog = true;
-                    }
-                }
-                if (test_bar(&h1_full[mp % kSH], (uint32_t)((mp / kSH) & 1))) {
-                    const int k = M.k, n = M.n, m = k >> 1;
-                    const bool opens = !(k & 1) && m < n;
-                    const int og = obase + m;  // global latent plane opened (k even) or continued
-                    if (!opens || og < 2 ||
-                        test_bar(&acc_free[og & 1], (uint32_t)(((og >> 1) - 1) & 1))) {
-                        tc::tc_fence_after();
-                        uint64_t dB;
-                        asm volatile("mov.b64 %0, %1;" : "=l"(dB) : "l"(dB0));
-                        const uint64_t dA = tc::sdesc(h1_a + (mp % kSH) * kH1Bytes, kKcBytes,
-                                                      2 * kRowBytes);
-                        if (k & 1) {
-                            issue_taps(tmem + (og & 1) * 16, dA, dB, 1, false, idesc);
-                        } else {
-                            if (m >= 1) {
-                                issue_taps(tmem + ((og - 1) & 1) * 16, dA, dB, 2, false, idesc);
-                                tc::mma_commit(&acc_full[(og - 1) & 1]);
-                            }
-                            if (opens) issue_taps(tmem + (og & 1) * 16, dA, dB, 0, true, idesc);
-                        }
-                        tc::mma_commit(&h1_free[mp % kSH]);
-                        mp++;
-                        if (M.k + 1 == 2 * M.n + 1) obase += M.n;
-                        M.next(S, lnz);
-                        prog = true;
-                    }
-                }
-                if (prog) {
-                    idle = 0;
-                } else if (++idle > kIdleLimit || *abrt) {
-                    ok = false;
-                }
+                tc::mma_commit(&h1_free[mp % kSH]);
+                if (M.k + 1 == 2 * M.n + 1) obase += M.n;
+                M.next(S, lnz);
             }
-            if (!ok) {
-                *abrt = 1;
-                // copies still in flight must land before the CTA leaves: wait
-                // (bounded, ignoring the flag) for every snapshot slot's last load
-                for (int s = (l_seq > kSS ? l_seq - kSS : 0); s < l_seq; s++)
-                    wait_bar(&snap_full[s % kSS], (uint32_t)((s / kSS) & 1), nullptr);
-            }
+            if (!ok) *abrt = 1;
             tc::mma_commit(&fin);
             if (!wait_bar(&fin, 0, nullptr)) *abrt = 1;
         }
-    } else if (warp <= 8) {
-        // ---------------- E1: two warpgroups, alternate h1 planes ----------------
+    } else if (warp <= 16) {
+        // ---------------- E1: two roles of 8 warps, alternate h1 planes ----------------
         // per plane: A tile rows = bf16(s / rms) of each h1 voxel's 2 x 2 x 2 patch;
-        // the producer's MMAs put W1 x0 into this warpgroup's TMEM columns; the
-        // epilogue adds b1, applies LeakyReLU, rounds to bf16 and stores h1
-        const int g = (warp - 1) >> 2, t = tid - 32 - 128 * g, q = warp & 3;
+        // the role's first thread puts W1 x0 into the role's TMEM columns; the
+        // epilogue adds b1, applies LeakyReLU, rounds to bf16 and stores h1.
+        // Role g = warps 1 + 8 g .. 8 + 8 g; a warp reads TMEM lanes 32 (warp % 4)
+        // .. + 31 and h1 channels 16 hc .. 16 hc + 15 (hc: its warpgroup in the role)
+        const int g = (warp - 1) >> 3, t = tid - 32 - kE1Threads * g, q = warp & 3;
+        const int hc = ((warp - 1) >> 2) & 1;
         uint8_t* at = atile + g * kATileBytes;
-        const uint32_t tcol = tmem + kE1Col + g * 160 + ((uint32_t)(q * 32) << 16);
-        float b1[32];
+        const uint32_t tcol = tmem + kE1Col + g * 160 + 16 * hc + ((uint32_t)(q * 32) << 16);
+        constexpr uint32_t idesc1 = tc::idesc_bf16(128, 32);
+        const uint64_t dW1 = tc::sdesc(tc::smem_u32(w1), 128, 256);
+        // b1 of this warp's 16 channels as pairs, and the slope as a pair:
+        // packed f32x2 adds and multiplies (IEEE single precision per lane)
+        uint64_t b1p[8];
 #pragma unroll
-        for (int c = 0; c < 32; c++) b1[c] = A.P[kOB1 + c];
+        for (int c = 0; c < 8; c++)
+            b1p[c] = f32x2::pack(A.P[kOB1 + 16 * hc + 2 * c], A.P[kOB1 + 16 * hc + 2 * c + 1]);
+        const uint64_t slope2 = f32x2::pack(kSlope, kSlope);
         const float inv_s = *A.inv_sigma;
+        // per item: this thread's h1 row offset in each M tile (16 bits each,
+        // two per word: every offset is below 2^15) and whether the row's
+        // voxel lies inside the h1 volume in x and y (bit mt)
+        uint32_t tile_off[3];
+        uint32_t in_xy = 0;
+        int cur_item = -1;
         PlaneCursor C;
         C.start(S, lnz);
         bool ok = true;
@@ -387,62 +417,128 @@ __global__ void __launch_bounds__(kThreads, 1)
             if ((j & 1) != g) continue;
             int cx, cy, z0, nz;
             item_coords(S, lnz, C.item, cx, cy, z0, nz);
+            if (C.item != cur_item) {
+                cur_item = C.item;
+                in_xy = 0;
+                tile_off[0] = tile_off[1] = tile_off[2] = 0;
+#pragma unroll
+                for (int mt = 0; mt < 5; mt++) {
+                    const int r = mt * 128 + q * 32 + lane;
+                    const int iy = r / HX, sl = r - iy * HX;
+                    const int ix = sl < 9 ? 2 * sl : 2 * sl - 17;
+                    const int hy = 32 * cy - 1 + iy, hx = 16 * cx - 1 + ix;
+                    tile_off[mt >> 1] |= (uint32_t)(iy * kRowBytes + sl * 16 + 2 * hc * kKcBytes)
+                                         << (16 * (mt & 1));
+                    if (r < NVOX && hy >= 0 && hy < A.h.ny && hx >= 0 && hx < A.h.nx)
+                        in_xy |= 1u << mt;
+                }
+            }
             const int hz = 2 * z0 - 1 + C.k;
             ok = wait_bar(&snap_full[j % kSS], (uint32_t)((j / kSS) & 1), abrt);
             if (!ok) break;
             const float* sp = snap + (j % kSS) * (kSnapBytes / 4);
-            for (int v = t; v < NVOX; v += 128) {
-                const int iy = v / HX, ix = v - iy * HX;
-                float x[8];
+            // A tile rows in h1 slot order: row 17 iy + slot. Unit (iy, p) reads
+            // the snapshot float4 at box x = 4 p, which holds the patch columns
+            // of h1 x positions 2 p - 1 (slot 8 + p; none for p = 0) and 2 p
+            // (slot p)
+            for (int u = t; u < HY * 9; u += kE1Threads) {
+                const int iy = u / 9, p = u - iy * 9;
+                float xe[8], xo[8];
 #pragma unroll
                 for (int dz = 0; dz < 2; dz++)
 #pragma unroll
                     for (int dy = 0; dy < 2; dy++) {
-                        const float2 p2 = *reinterpret_cast<const float2*>(
-                            sp + (dz * SYR + 2 * iy + dy) * SX + 2 + 2 * ix);
-                        x[dz * 4 + dy * 2] = p2.x * inv_s;
-                        x[dz * 4 + dy * 2 + 1] = p2.y * inv_s;
+                        const float4 p4 = *reinterpret_cast<const float4*>(
+                            sp + (dz * SYR + 2 * iy + dy) * SX + 4 * p);
+                        xo[dz * 4 + dy * 2] = p4.x * inv_s;
+                        xo[dz * 4 + dy * 2 + 1] = p4.y * inv_s;
+                        xe[dz * 4 + dy * 2] = p4.z * inv_s;
+                        xe[dz * 4 + dy * 2 + 1] = p4.w * inv_s;
                     }
-                *reinterpret_cast<uint4*>(at + v * 16) = tc::pack8(x);
+                *reinterpret_cast<uint4*>(at + (iy * HX + p) * 16) = tc::pack8(xe);
+                if (p > 0) *reinterpret_cast<uint4*>(at + (iy * HX + 8 + p) * 16) = tc::pack8(xo);
             }
             tc::fence_proxy_async();
             bar_arrive(&snap_free[j % kSS]);
             bar_arrive(&e1a_full[g]);
-            ok = wait_bar(&e1_done[g], (uint32_t)((j >> 1) & 1), abrt);
+            bool issued = false;
+            if (t == 0) {
+                // E1 of plane j once all 128 rows are written: 5 M tiles of
+                // 128 voxels, K = 16 (8 inputs + 8 zeros)
+                ok = wait_bar(&e1a_full[g], (uint32_t)((j >> 1) & 1), abrt);
+                if (ok) {
+                    issued = true;
+                    tc::tc_fence_after();
+                    const uint32_t a0 = tc::smem_u32(at);
+#pragma unroll
+                    for (int mt = 0; mt < 5; mt++)
+                        tc::mma_bf16(tmem + kE1Col + g * 160 + mt * 32,
+                                     tc::sdesc(a0 + mt * 2048, 128, 128), dW1, idesc1, 0u);
+                    tc::mma_commit(&e1_done[g]);
+                }
+            }
+            if (ok) ok = wait_bar(&e1_done[g], (uint32_t)((j >> 1) & 1), abrt);
+            // the MMAs must be done with the tile and the accumulator before
+            // an aborting CTA frees its tensor memory: wait, ignoring the flag
+            if (!ok && issued) wait_bar(&e1_done[g], (uint32_t)((j >> 1) & 1), nullptr);
             if (ok && j >= kSH) ok = wait_bar(&h1_free[j % kSH], (uint32_t)((j / kSH - 1) & 1), abrt);
             if (!ok) break;
             tc::tc_fence_after();
             uint8_t* hp = h1 + (j % kSH) * kH1Bytes;
             const bool zin = hz >= 0 && hz < A.h.nz;
-#pragma unroll 1
-            for (int mt = 0; mt < 5; mt++) {
-                const int v0 = mt * 128 + q * 32;
-                if (v0 >= NVOX) break;  // warp-uniform
-                float acc[32];
-                tc::tmem_ld16(tcol + mt * 32, acc);
-                tc::tmem_ld16(tcol + mt * 32 + 16, acc + 16);
-                const int v = v0 + lane;
-                if (v < NVOX) {
-                    const int iy = v / HX, ix = v - iy * HX;
-                    const int hy = 32 * cy - 1 + iy, hx = 16 * cx - 1 + ix;
-                    const bool in = zin && hy >= 0 && hy < A.h.ny && hx >= 0 && hx < A.h.nx;
-                    uint8_t* dst = hp + iy * kRowBytes + x_slot(ix) * 16;
+            // one M tile's 16 channels: b1, LeakyReLU as max(h, slope h) (the
+            // same bits as the select form for 0 < slope < 1), bf16, two
+            // 16-byte stores; consecutive lanes hold consecutive slots, so the
+            // stores are conflict-free
+            auto store_tile = [&](int mt, const uint32_t* acc) {
+                if (mt * 128 + q * 32 + lane >= NVOX) return;
+                const bool in = zin && ((in_xy >> mt) & 1u);
+                uint8_t* dst = hp + ((tile_off[mt >> 1] >> (16 * (mt & 1))) & 0xFFFFu);
+                uint32_t w[8];  // every value first, then the two stores
 #pragma unroll
-                    for (int kc = 0; kc < 4; kc++) {
-                        float hv[8];
-#pragma unroll
-                        for (int c = 0; c < 8; c++) hv[c] = lrelu(acc[8 * kc + c] + b1[8 * kc + c]);
-                        *reinterpret_cast<uint4*>(dst + kc * kKcBytes) =
-                            in ? tc::pack8(hv) : make_uint4(0u, 0u, 0u, 0u);
-                    }
+                for (int c = 0; c < 8; c++) {
+                    const uint64_t h = f32x2::add(
+                        f32x2::pack(__uint_as_float(acc[2 * c]), __uint_as_float(acc[2 * c + 1])),
+                        b1p[c]);
+                    const uint64_t sh = f32x2::mul(h, slope2);
+                    float h0, h1, s0, s1;
+                    f32x2::unpack(h, h0, h1);
+                    f32x2::unpack(sh, s0, s1);
+                    w[c] = in ? tc::pack2(fmaxf(h0, s0), fmaxf(h1, s1)) : 0u;
                 }
+                *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4*>(dst + kKcBytes) = make_uint4(w[4], w[5], w[6], w[7]);
+            };
+            // tiles 0-3 hold rows of every warp (row 384 + 127 < 561); tile 4
+            // only those of the warps whose rows start below 561. Each tile
+            // after the first two loads while the one before it is stored (a
+            // loaded register becomes readable a few hundred cycles after the
+            // load is issued)
+            const bool t4 = 4 * 128 + q * 32 < NVOX;  // warp-uniform
+            uint32_t x0[16], x1[16], x2[16];
+            tmem_ld16_nw(tcol, x0);
+            tmem_ld16_nw(tcol + 32, x1);
+            tmem_wait_regs(x0);
+            tmem_wait_regs(x1);
+            tmem_ld16_nw(tcol + 64, x2);
+            store_tile(0, x0);
+            store_tile(1, x1);
+            tmem_wait_regs(x2);
+            tmem_ld16_nw(tcol + 96, x0);
+            store_tile(2, x2);
+            tmem_wait_regs(x0);
+            if (t4) tmem_ld16_nw(tcol + 128, x1);
+            store_tile(3, x0);
+            if (t4) {
+                tmem_wait_regs(x1);
+                store_tile(4, x1);
             }
             tc::tc_fence_before();
             tc::fence_proxy_async();
             bar_arrive(&h1_full[j % kSH]);
         }
-    } else {
-        // ---------------- latent epilogue: warpgroup 3 ----------------
+    } else if (warp <= 20) {
+        // ---------------- latent epilogue: warps 17-20 ----------------
         const int row = tid & 127, ly = row >> 3, lx = row & 7;
         const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
         float b2[16];
@@ -473,6 +569,29 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
+    } else if (lane == 0) {
+        // ---------------- snapshot loader: warp 21 ----------------
+        // each h1 plane's two snapshot planes into the next ring slot once
+        // the role that used the slot last has built its A tile from it
+        PlaneCursor L;
+        L.start(S, lnz);
+        int l_seq = 0;
+        for (; L.valid(S); l_seq++, L.next(S, lnz)) {
+            const int slot = l_seq % kSS;
+            if (l_seq >= kSS &&
+                !wait_bar(&snap_free[slot], (uint32_t)((l_seq / kSS - 1) & 1), abrt))
+                break;
+            int lcx, lcy, lz0, lnzi;
+            item_coords(S, lnz, L.item, lcx, lcy, lz0, lnzi);
+            bar_expect(&snap_full[slot], kSnapBytes);
+            tma_snap(snap + slot * (kSnapBytes / 4), &map, 32 * lcx - 4, 64 * lcy - 2,
+                     2 * (2 * lz0 - 1 + L.k), &snap_full[slot]);
+        }
+        // every copy must land before the CTA leaves (after an abort some were
+        // never waited for): wait, bounded and ignoring the flag, for each
+        // slot's last load; a completed one answers at once
+        for (int q = (l_seq > kSS ? l_seq - kSS : 0); q < l_seq; q++)
+            wait_bar(&snap_full[q % kSS], (uint32_t)((q / kSS) & 1), nullptr);
     }
     tc::tc_fence_before();
     __syncthreads();

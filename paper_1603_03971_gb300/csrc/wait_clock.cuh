@@ -21,4 +21,21 @@ __device__ __forceinline__ bool wait_expired(long long poll, unsigned long long 
     return (poll & 255) == 255 && wait_now() - t0 > kWaitNs;
 }
 
+// one poll of an mbarrier phase (shared-memory address a) that lets the
+// thread sleep until the phase completes or suspend_ns nanoseconds pass:
+// a thread that waits long stays off the issue slots and the shared-memory
+// pipe instead of re-polling
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t a, uint32_t parity,
+                                                    uint32_t suspend_ns) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity), "r"(suspend_ns)
+        : "memory");
+    return done != 0;
+}
+
 }  // namespace rtm
