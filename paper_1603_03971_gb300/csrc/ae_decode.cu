@@ -16,8 +16,9 @@
 // started at plane z + tz, row (1 + ty), column (1 + tx): a descriptor with a
 // shifted start address.
 //
-// Roles: warp 8 (one thread) issues the TMA plane loads (up to kLook planes
-// ahead) and the MMAs into one of two accumulator buffers (2 x 256 columns);
+// Roles: warp 9 (one thread) issues the TMA plane loads, each as soon as its
+// ring slot is free; warp 8 (one thread) the MMAs into one of two
+// accumulator buffers (2 x 256 columns);
 // warpgroup 0 finishes even planes, warpgroup 1 odd planes, four parities at
 // a time: tcgen05.ld of their accumulators (one row per thread),
 // LeakyReLU(acc + b3) rounded to bfloat16 (as the training decoder rounds
@@ -52,14 +53,13 @@ constexpr int kHalfBytes = 2944;               // one 8-channel half plane (2880
 constexpr int kPlaneBytes = 2 * kHalfBytes;
 constexpr int kTmaBytes = 2 * HX * HY * 16;    // bytes one plane load delivers
 constexpr int kSlots = 9;                      // plane ring
-constexpr int kLook = kSlots - 4;              // planes loaded beyond the newest one needed
 constexpr int kW3Bytes = 64 * 1024;            // 64 B operands (parity, tap): 32 x 16, 1 KB each
 constexpr int kA2Bytes = 128 * 32 * 2;          // D2 A operand: 128 rows x 32 channels, bf16
 // W3 operands, plane ring, b3 (128 B), the D2 B operand W4 (16 x 32 bf16,
 // 1 KB), four D2 A operands per epilogue warpgroup: > half an SM, 1 CTA
 constexpr int kSmem = 128 + kW3Bytes + kSlots * kPlaneBytes + 128 + 1024 + 2 * 4 * kA2Bytes;
 constexpr int kTmemCols = 512;
-constexpr int kThreads = 288;
+constexpr int kThreads = 320;
 constexpr long long kLimit = 1LL << 24;
 constexpr uint32_t kSuspendNs = 20000;  // longest sleep of one poll (woken by the phase)
 
@@ -120,18 +120,27 @@ __device__ __forceinline__ void tma_plane(uint8_t* dst, const CUtensorMap* map, 
         "r"(tc::smem_u32(bar))
         : "memory");
 }
-// 16 columns of this warp's lanes, without waiting
-__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, float* out) {
-    uint32_t r[16];
+// 16 columns of this warp's lanes into r, without waiting: the registers
+// must not be read before a tmem_wait_regs16 that names them
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t* r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
           "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 16; i++) out[i] = __uint_as_float(r[i]);
+        : "r"(taddr)
+        : "memory");
+}
+// wait for this thread's TMEM loads; the 16 registers are operands, so no
+// read of them can be scheduled before the wait
+__device__ __forceinline__ void tmem_wait_regs16(uint32_t* r) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
 }
 // all 128 threads of a warpgroup (named barrier id) agree: true only if v is
 // true in every one of them; also a barrier of the warpgroup
@@ -147,19 +156,14 @@ __device__ __forceinline__ bool wg_all(bool v, int id) {
         : "memory");
     return r != 0;
 }
-// 8 columns of this warp's lanes, without waiting
-__device__ __forceinline__ void tmem_ld8_nw(uint32_t taddr, float* out) {
-    uint32_t r[8];
+// 8 columns of this warp's lanes into r, without waiting (as tmem_ld16_nw)
+__device__ __forceinline__ void tmem_ld8_nw(uint32_t taddr, uint32_t* r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7])
-        : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 8; i++) out[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_wait_ld() {
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        : "r"(taddr)
+        : "memory");
 }
 
 // byte offset of (row o, k) in a 32 x 16 K-major operand (LBO 128, SBO 256)
@@ -235,43 +239,18 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == 8) {
         if (lane == 0) {
-            // ---------------- producer: plane loads and MMAs ----------------
+            // ---------------- MMA issuer ----------------
             constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
             const uint32_t ring_a = tc::smem_u32(ring);
             const uint64_t dB0 = tc::sdesc(tc::smem_u32(w3), 128, 256);
-            // load cursor: k-th item of this CTA, plane j of that item, global sequence
-            int l_k = 0, l_j = 0, l_seq = 0, waited = 0;
             int out = 0, base_seq = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < S.nitems && ok; item += gridDim.x) {
                 int cx, cy, z0, nz;
                 item_coords(S, lnz, item, cx, cy, z0, nz);
                 for (int zi = 0; zi < nz && ok; zi++) {
-                    const int target = base_seq + zi + 2 + kLook;
-                    while (ok && l_seq <= target) {
-                        const int litem = blockIdx.x + l_k * gridDim.x;
-                        if (litem >= S.nitems) break;
-                        int lcx, lcy, lz0, lnzi;
-                        item_coords(S, lnz, litem, lcx, lcy, lz0, lnzi);
-                        const int slot = l_seq % kSlots;
-                        if (l_seq >= kSlots)
-                            ok = wait_bar(&freed[slot], (uint32_t)((l_seq / kSlots - 1) & 1), abrt);
-                        if (!ok) break;
-                        bar_expect(&full[slot], kTmaBytes);
-                        uint8_t* dst = ring + slot * kPlaneBytes;
-                        for (int kc = 0; kc < 2; kc++)
-                            tma_plane(dst + kc * kHalfBytes, &map, kc, lcx * TX - 1, lcy * TY - 1,
-                                      lz0 - 1 + l_j, &full[slot]);
-                        l_seq++;
-                        if (++l_j == lnzi + 2) {
-                            l_j = 0;
-                            l_k++;
-                        }
-                    }
-                    for (int s = base_seq + zi; s <= base_seq + zi + 2 && ok; s++) {
+                    for (int s = base_seq + zi; s <= base_seq + zi + 2 && ok; s++)
                         ok = wait_bar(&full[s % kSlots], (uint32_t)((s / kSlots) & 1), abrt);
-                        if (ok && s >= waited) waited = s + 1;
-                    }
                     const int b = out & 1, u = out >> 1;
                     if (ok && u >= 1) ok = wait_bar(&acc_free[b], (uint32_t)((u - 1) & 1), abrt);
                     if (!ok) break;
@@ -312,14 +291,37 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 base_seq += nz + 2;
             }
-            if (!ok) {
-                *abrt = 1;
-                // loads still in flight must land before the CTA leaves
-                for (int s = waited; s < l_seq; s++)
-                    wait_bar(&full[s % kSlots], (uint32_t)((s / kSlots) & 1), nullptr);
-            }
+            if (!ok) *abrt = 1;
             tc::mma_commit(&fin);
             if (!wait_bar(&fin, 0, nullptr)) *abrt = 1;
+        }
+    } else if (warp == 9) {
+        if (lane == 0) {
+            // ---------------- plane loader ----------------
+            // every latent plane of every item (with its z halo) into the next
+            // ring slot as soon as the MMAs that read the slot last are done
+            int l_seq = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < S.nitems && ok; item += gridDim.x) {
+                int lcx, lcy, lz0, lnzi;
+                item_coords(S, lnz, item, lcx, lcy, lz0, lnzi);
+                for (int l_j = 0; l_j < lnzi + 2; l_j++, l_seq++) {
+                    const int slot = l_seq % kSlots;
+                    if (l_seq >= kSlots)
+                        ok = wait_bar(&freed[slot], (uint32_t)((l_seq / kSlots - 1) & 1), abrt);
+                    if (!ok) break;
+                    bar_expect(&full[slot], kTmaBytes);
+                    uint8_t* dst = ring + slot * kPlaneBytes;
+                    for (int kc = 0; kc < 2; kc++)
+                        tma_plane(dst + kc * kHalfBytes, &map, kc, lcx * TX - 1, lcy * TY - 1,
+                                  lz0 - 1 + l_j, &full[slot]);
+                }
+            }
+            // every copy must land before the CTA leaves (after an abort some
+            // were never waited for): wait, bounded and ignoring the flag, for
+            // each slot's last load; a completed one answers at once
+            for (int q = (l_seq > kSlots ? l_seq - kSlots : 0); q < l_seq; q++)
+                wait_bar(&full[q % kSlots], (uint32_t)((q / kSlots) & 1), nullptr);
         }
     } else {
         // ---------------- epilogue warpgroups ----------------
@@ -354,12 +356,21 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
                     for (int qy = 0; qy < 2; qy++) {
                         const int qzy = qz * 2 + qy;
+                        uint32_t r0[32], r1[32];
+                        tmem_ld16_nw(tb + (qzy * 2) * 32, r0);
+                        tmem_ld16_nw(tb + (qzy * 2) * 32 + 16, r0 + 16);
+                        tmem_ld16_nw(tb + (qzy * 2 + 1) * 32, r1);
+                        tmem_ld16_nw(tb + (qzy * 2 + 1) * 32 + 16, r1 + 16);
+                        tmem_wait_regs16(r0);
+                        tmem_wait_regs16(r0 + 16);
+                        tmem_wait_regs16(r1);
+                        tmem_wait_regs16(r1 + 16);
                         float a0[32], a1[32];
-                        tmem_ld16_nw(tb + (qzy * 2) * 32, a0);
-                        tmem_ld16_nw(tb + (qzy * 2) * 32 + 16, a0 + 16);
-                        tmem_ld16_nw(tb + (qzy * 2 + 1) * 32, a1);
-                        tmem_ld16_nw(tb + (qzy * 2 + 1) * 32 + 16, a1 + 16);
-                        tmem_wait_ld();
+#pragma unroll
+                        for (int i = 0; i < 32; i++) {
+                            a0[i] = __uint_as_float(r0[i]);
+                            a1[i] = __uint_as_float(r1[i]);
+                        }
 #pragma unroll
                         for (int c4 = 0; c4 < 8; c4++) {
                             const float4 bb = b3v[c4];
@@ -405,10 +416,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                     d2_phase++;
                     if (row == 0) d2_pending = false;
                     tc::tc_fence_after();
+                    uint32_t ry[32];
+#pragma unroll
+                    for (int p = 0; p < 4; p++) tmem_ld8_nw(tb + (qz * 4 + p) * 32, ry + 8 * p);
+                    tmem_wait_regs16(ry);
+                    tmem_wait_regs16(ry + 16);
                     float y[4][8];
 #pragma unroll
-                    for (int p = 0; p < 4; p++) tmem_ld8_nw(tb + (qz * 4 + p) * 32, y[p]);
-                    tmem_wait_ld();
+                    for (int p = 0; p < 4; p++)
+#pragma unroll
+                        for (int i = 0; i < 8; i++) y[p][i] = __uint_as_float(ry[8 * p + i]);
                     if (valid) {
 #pragma unroll
                         for (int qy = 0; qy < 2; qy++) {
