@@ -579,6 +579,24 @@ rtm_status rtm_set_tuning(int32_t radius, int32_t zchunk, int32_t variant);
  * the per-mode timings of its trials. Applies to the single-shot calls. */
 rtm_status rtm_set_tuning_mode(int32_t radius, int32_t mode, int32_t zchunk);
 
+/* Host-injected wait failure for testing the timeout path of the kernels
+ * with mbarrier rings: kernel RTM_STALL_STENCIL (the TMA stencil's plain
+ * forward step with 8-row tiles, tuning variant 3, as a separate kernel
+ * instance: the others carry no code for it) or RTM_STALL_ENCODER (the
+ * z-marching codec encoder); plane >= 0 arms a
+ * one-shot stall of that kernel's next launch: block 0's copy of the plane
+ * `plane` planes before the last one it copies (0: the last; the encoder
+ * takes 0-2) expects 16 bytes more than it delivers, so the bounded wait
+ * for it runs out after about 2 s; the block raises its abort flag, waits
+ * (bounded) for every copy it issued and leaves, and the call's status word
+ * reads RTM_ERR_TIMEOUT (rtm_check). Every copy lands, and no later copy
+ * reuses the stalled ring slot (a wait for a later phase of a barrier whose
+ * phase never completes would pass at once); nothing faults. -1 disarms.
+ * Returns RTM_ERR_INVALID for an unknown kernel. */
+#define RTM_STALL_STENCIL 0
+#define RTM_STALL_ENCODER 1
+rtm_status rtm_set_test_stall(int32_t kernel, int32_t plane);
+
 /* Enable (1) or disable (0) per-launch CUDA-event timing of the stencil
  * kernels. While enabled, each API call synchronises its stream on return. */
 rtm_status rtm_set_timing(int32_t enable);

@@ -358,6 +358,16 @@ def set_tuning_mode(radius: int, mode: str, zchunk: int):
     call("rtm_set_tuning_mode", radius, MODE_SLOTS[mode], zchunk)
 
 
+STALL_STENCIL, STALL_ENCODER = 0, 1
+
+
+def set_test_stall(kernel: int, plane: int):
+    """Arm (plane >= 0) or disarm (-1) a one-shot wait failure in the next
+    launch of the TMA stencil (``STALL_STENCIL``) or the codec encoder
+    (``STALL_ENCODER``): the call then reports RTM_ERR_TIMEOUT (testing)."""
+    call("rtm_set_test_stall", kernel, plane)
+
+
 def set_timing(enable: bool):
     call("rtm_set_timing", 1 if enable else 0)
 

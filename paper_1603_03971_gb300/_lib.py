@@ -82,6 +82,7 @@ SIGNATURES = {
     "rtm_forward_noalloc": (ctypes.c_int, [_P, _vp, _vp, _vp, _vp, _vp]),
     "rtm_set_tuning": (ctypes.c_int, [_i32, _i32, _i32]),
     "rtm_set_tuning_mode": (ctypes.c_int, [_i32, _i32, _i32]),
+    "rtm_set_test_stall": (ctypes.c_int, [_i32, _i32]),
     "rtm_offgrid_taps": (_sz, [_P, _vp, _i32, _vp, _vp, _sz]),
     "rtm_forward_offgrid": (ctypes.c_int, [_P, _vp, _vp, _vp, _vp, _sz, _vp, _vp]),
     "rtm_shot_offgrid": (ctypes.c_int, [_P, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _vp]),

@@ -60,8 +60,10 @@
 
 #include <algorithm>
 
+#include "../../include/rtm.h"
 #include "ae_internal.h"
 #include "packed_f32x2.cuh"
+#include "rtm_internal.h"
 #include "tc_gemm.cuh"
 #include "tma_encode.h"
 #include "wait_clock.cuh"
@@ -109,6 +111,8 @@ struct EncArgs {
     const float* inv_sigma;
     bf16* lat;
     Dims3 l, h;
+    int stall;  // >= 0: CTA 0's copy of the h1 plane that many before its last
+                // expects 16 bytes too many (test)
 };
 
 __device__ __forceinline__ void item_coords(const Sched& S, int lnz, int item, int& cx, int& cy,
@@ -573,6 +577,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- snapshot loader: warp 21 ----------------
         // each h1 plane's two snapshot planes into the next ring slot once
         // the role that used the slot last has built its A tile from it
+        int np = 0;  // h1 planes of this CTA
+        for (int item = blockIdx.x; item < S.nitems; item += gridDim.x) {
+            int cx, cy, z0, nz;
+            item_coords(S, lnz, item, cx, cy, z0, nz);
+            np += 2 * nz + 1;
+        }
         PlaneCursor L;
         L.start(S, lnz);
         int l_seq = 0;
@@ -583,7 +593,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             int lcx, lcy, lz0, lnzi;
             item_coords(S, lnz, L.item, lcx, lcy, lz0, lnzi);
-            bar_expect(&snap_full[slot], kSnapBytes);
+            // a test-armed stall: this copy's phase never completes, so the
+            // wait for it runs out (rtm_set_test_stall). It is one of the
+            // CTA's last kSS copies: no later copy reuses its slot, so no
+            // wait can take a later phase of its mbarrier for the stuck one
+            const bool stalled =
+                A.stall >= 0 && A.stall < kSS && l_seq == np - 1 - A.stall && blockIdx.x == 0;
+            bar_expect(&snap_full[slot], kSnapBytes + (stalled ? 16u : 0u));
             tma_snap(snap + slot * (kSnapBytes / 4), &map, 32 * lcx - 4, 64 * lcy - 2,
                      2 * (2 * lz0 - 1 + L.k), &snap_full[slot]);
         }
@@ -660,7 +676,7 @@ cudaError_t ae_encode_march(const float* P, const ae::Vol& in, const float* inv_
         }
     }
     S.nitems = (int)(ncol * ((l.nz + S.zc - 1) / S.zc));
-    EncArgs a{P, inv_sigma, lat, l, h};
+    EncArgs a{P, inv_sigma, lat, l, h, take_test_stall(RTM_STALL_ENCODER)};
     const int grid = std::min(nsm, S.nitems);
     k_encode_march<<<grid, kThreads, kSmem, s>>>(a, map, S, status);
     return cudaGetLastError();

@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -61,6 +62,9 @@ int g_zchunk[kMaxRadius + 1] = {0};
 // per stencil mode (statistics slot): slab height, 0 = the radius's general one
 int g_zchunk_mode[kMaxRadius + 1][MODE_COUNT] = {{0}};
 int g_variant[kMaxRadius + 1] = {0};
+// one-shot stalls armed by rtm_set_test_stall (RTM_STALL_*), -1 = none
+constexpr int kStallKernels = 2;
+std::atomic<int> g_test_stall[kStallKernels] = {{-1}, {-1}};
 bool g_timing = false;
 rtm_stats g_stats;
 
@@ -825,6 +829,12 @@ int rtm::tuning_variant(int radius) {
     return g_variant[radius];
 }
 
+int rtm::take_test_stall(int kernel) {
+    if (kernel < 0 || kernel >= kStallKernels) return -1;
+    if (g_test_stall[kernel].load(std::memory_order_relaxed) < 0) return -1;
+    return g_test_stall[kernel].exchange(-1);
+}
+
 int rtm::set_error(int code, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -1255,6 +1265,13 @@ rtm_status rtm_set_tuning(int32_t radius, int32_t zchunk, int32_t variant) {
     g_zchunk[radius] = zchunk;
     g_variant[radius] = variant;
     for (int m = 0; m < MODE_COUNT; m++) g_zchunk_mode[radius][m] = 0;
+    return RTM_OK;
+}
+
+rtm_status rtm_set_test_stall(int32_t kernel, int32_t plane) {
+    if (kernel < 0 || kernel >= kStallKernels)
+        return (rtm_status)rtm::set_error(RTM_ERR_INVALID, "unknown stall kernel %d", kernel);
+    g_test_stall[kernel].store(plane < 0 ? -1 : plane);
     return RTM_OK;
 }
 

@@ -173,5 +173,8 @@ int tuning_variant(int radius);
 // z-slab height chosen by rtm_set_tuning for a radius (0: automatic); with a
 // mode, that mode's height from rtm_set_tuning_mode where one is set
 int tuning_zchunk(int radius, int mode = -1);
+// the plane armed by rtm_set_test_stall for a kernel (RTM_STALL_*), or -1;
+// taking it disarms it, so only the next launch stalls
+int take_test_stall(int kernel);
 
 }  // namespace rtm

@@ -35,6 +35,7 @@
 
 #include <mutex>
 
+#include "../../include/rtm.h"
 #include "packed_f32x2.cuh"
 #include "rtm_internal.h"
 #include "stencil_common.cuh"
@@ -254,9 +255,13 @@ constexpr bool rings_fit() {
            228 * 1024;
 }
 
-template <int R, int MODE, int BY>
+// STALL: the instance that takes a test-armed stall (rtm_set_test_stall);
+// compiled only for the forward step with 8-row tiles, so that no other
+// instance carries its code
+template <int R, int MODE, int BY, bool STALL = false>
 __global__ void __launch_bounds__(16 * BY, (tma_min_blocks<R, MODE, BY>()))
-    k_stencil_tma(const __grid_constant__ StepArgs A, const __grid_constant__ TmaMaps M, int* status) {
+    k_stencil_tma(const __grid_constant__ StepArgs A, const __grid_constant__ TmaMaps M, int* status,
+                  int stall) {
     constexpr int V = points_per_thread<R, BY>();
     using T = TmaTile<R, V, BY>;
     using VT = Vec<V>;
@@ -313,7 +318,16 @@ __global__ void __launch_bounds__(16 * BY, (tma_min_blocks<R, MODE, BY>()))
         a_end = p + 1;
         const int slot = (p - zb) % C::SA;
         float* base = aring + slot * C::NAH * C::APLANE;
-        bar_expect(&abar[slot], C::NAH * C::APLANE * 4);
+        uint32_t extra = 0;
+        if constexpr (STALL) {
+            // block 0's copy of the plane `stall` planes before its last
+            // expects 16 bytes that never arrive, so the wait for it runs
+            // out. No later copy reuses that slot, so no wait can take a
+            // later phase of its mbarrier for the stuck one
+            if (p == ze - 1 - stall && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)
+                extra = 16;
+        }
+        bar_expect(&abar[slot], C::NAH * C::APLANE * 4 + extra);
         tma3(base, &M.prev, x0, y0, p, &abar[slot]);
         tma3(base + C::APLANE, &M.c, x0, y0, p, &abar[slot]);
         if constexpr (C::SPLIT) tma3(base + NA * C::APLANE, &M.uh, x0, y0, p + R, &abar[slot]);
@@ -596,6 +610,15 @@ cudaError_t encode_map(CUtensorMap* m, const float* base, int nx, int ny, int nz
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// dynamic shared memory and carveout of a TMA stencil instance
+template <class K>
+cudaError_t set_tma_attrs(K kernel, int smem) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                cudaSharedmemCarveoutMaxShared);
+}
+
 template <int R, int MODE, int BY>
 cudaError_t launch_tma_t(const StepArgs& a, int* status, cudaStream_t s) {
     using T = TmaTile<R, points_per_thread<R, BY>(), BY>;
@@ -603,12 +626,7 @@ cudaError_t launch_tma_t(const StepArgs& a, int* status, cudaStream_t s) {
     static_assert(rings_fit<R, MODE, BY>(), "rings do not fit the resident blocks");
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_stencil_tma<R, MODE, BY>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_stencil_tma<R, MODE, BY>,
-                                 cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared);
+        cudaError_t e = set_tma_attrs(k_stencil_tma<R, MODE, BY>, smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -637,7 +655,20 @@ cudaError_t launch_tma_t(const StepArgs& a, int* status, cudaStream_t s) {
               (a.zend - a.zorg + a.zchunk - 1) / a.zchunk);
     if (a.xorg % 4 || a.xend <= a.xorg || a.yend <= a.yorg || a.zend <= a.zorg)
         return cudaErrorInvalidValue;
-    k_stencil_tma<R, MODE, BY><<<grid, block, smem, s>>>(a, M, status);
+    if constexpr (MODE == MODE_FWD && BY == 8) {
+        const int stall = take_test_stall(RTM_STALL_STENCIL);
+        if (stall >= 0) {
+            static bool attr_stall = false;
+            if (!attr_stall) {
+                cudaError_t e = set_tma_attrs(k_stencil_tma<R, MODE, BY, true>, smem);
+                if (e != cudaSuccess) return e;
+                attr_stall = true;
+            }
+            k_stencil_tma<R, MODE, BY, true><<<grid, block, smem, s>>>(a, M, status, stall);
+            return cudaGetLastError();
+        }
+    }
+    k_stencil_tma<R, MODE, BY><<<grid, block, smem, s>>>(a, M, status, -1);
     return cudaGetLastError();
 }
 
