@@ -4,8 +4,10 @@
 //
 // Work item: a column of 8 x 16 latent voxels (x, y) over a range of z. For
 // each latent plane z the 128 voxels of the column are the M = 128 rows of
-// 8 parities x 8 taps = 64 tcgen05.mma (K = 16 input channels each, N = 32
-// output channels), accumulated per parity into tensor memory.
+// the 8 parities x 8 taps of D1 (K = 16 input channels each, N = 32 output
+// channels), accumulated per parity into tensor memory: 52 tcgen05.mma,
+// since in all but the first tap group the two parities of an x pair that
+// read the window at x offset 0 share one N = 64 MMA.
 //
 // The A operands are never gathered. TMA copies each latent plane of the
 // column with a one-voxel halo (10 x 18 voxels, zeros outside the grid) into
@@ -89,6 +91,15 @@ __device__ __forceinline__ void taps(int q, int tau, int& t, int& k) {
 }
 
 __device__ __forceinline__ float lrelu(float a) { return a > 0.f ? a : kSlope * a; }
+
+// KB block of the B operand of (parity q, tap tau) in the W3 table: per
+// x-parity pair m = q >> 1 and tap group g = tau >> 1 (z, y tap bits), four
+// blocks [q1 tap x 0, q0 tap x 0, q1 tap x 1, q0 tap x 1] (q0 = 2 m,
+// q1 = 2 m + 1), so that q0's x-offset-0 tap (x tap 0) and q1's (x tap 1)
+// are one 64-row operand
+__host__ __device__ constexpr int w3_block(int q, int tau) {
+    return (q >> 1) * 16 + (tau >> 1) * 4 + (tau & 1) * 2 + (1 - (q & 1));
+}
 
 __device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(b)),
@@ -218,7 +229,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         float w[8];
 #pragma unroll
         for (int e = 0; e < 8; e++) w[e] = d.P[kOW3 + o * 1024 + ktap * 16 + 8 * j + e];
-        *reinterpret_cast<uint4*>(w3 + t * 1024 + b_off(o, 8 * j)) = tc::pack8(w);
+        *reinterpret_cast<uint4*>(w3 + w3_block(q, tau) * 1024 + b_off(o, 8 * j)) =
+            tc::pack8(w);
     }
     // W4[e][c] (e = (ez, ey, ex), c = channel) as rows e of a 16 x 32 K-major
     // bf16 operand, rows 8..15 zero
@@ -240,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 8) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
+            constexpr uint32_t idesc = tc::idesc_bf16(128, 32), idesc64 = tc::idesc_bf16(128, 64);
             const uint32_t ring_a = tc::smem_u32(ring);
             const uint64_t dB0 = tc::sdesc(tc::smem_u32(w3), 128, 256);
             int out = 0, base_seq = 0;
@@ -266,18 +278,34 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // out of the loop into registers
                     uint64_t dB;
                     asm volatile("mov.b64 %0, %1;" : "=l"(dB) : "l"(dB0));
+                    // per x-parity pair (q0 = 2 m, q1 = 2 m + 1) and tap group
+                    // (tz', ty'): q0 reads x offsets 0 (x tap 0) and -1 (x tap 1),
+                    // q1 reads +1 (x tap 0) and 0 (x tap 1). In every group but
+                    // the first the two x-offset-0 taps are one N = 64 MMA into
+                    // both parities' columns, issued between q1's x tap 0 and
+                    // q0's x tap 1, so every parity sums its taps in tap order;
+                    // the first group runs as four MMAs, the first of each
+                    // parity overwriting its accumulator. 52 MMAs per plane
 #pragma unroll
-                    for (int q = 0; q < 8; q++) {
+                    for (int m = 0; m < 4; m++) {
+                        const uint32_t c0 = tmem + b * 256 + (2 * m) * 32, c1 = c0 + 32;
 #pragma unroll
-                        for (int tau = 0; tau < 8; tau++) {
-                            int tz, kz, ty, ky, tx, kx;
-                            taps(q >> 2, tau >> 2, tz, kz);
-                            taps((q >> 1) & 1, (tau >> 1) & 1, ty, ky);
-                            taps(q & 1, tau & 1, tx, kx);
-                            tc::mma_bf16(tmem + b * 256 + q * 32,
-                                         dA[1 + tz] + (uint64_t)((1 + ty) * HX + (1 + tx)),
-                                         dB + (uint64_t)((q * 8 + tau) * 64), idesc,
-                                         tau > 0 ? 1u : 0u);
+                        for (int g = 0; g < 4; g++) {
+                            int tz, kz, ty, ky;
+                            taps(m >> 1, g >> 1, tz, kz);
+                            taps(m & 1, g & 1, ty, ky);
+                            const uint64_t a = dA[1 + tz] + (uint64_t)((1 + ty) * HX);
+                            const uint64_t bg = dB + (uint64_t)((m * 16 + g * 4) * 64);
+                            if (g == 0) {
+                                tc::mma_bf16(c0, a + 1, bg + 64, idesc, 0u);       // q0, x tap 0
+                                tc::mma_bf16(c0, a + 0, bg + 3 * 64, idesc, 1u);   // q0, x tap 1
+                                tc::mma_bf16(c1, a + 2, bg, idesc, 0u);            // q1, x tap 0
+                                tc::mma_bf16(c1, a + 1, bg + 2 * 64, idesc, 1u);   // q1, x tap 1
+                            } else {
+                                tc::mma_bf16(c1, a + 2, bg, idesc, 1u);            // q1, x tap 0
+                                tc::mma_bf16(c0, a + 1, bg + 64, idesc64, 1u);     // both, offset 0
+                                tc::mma_bf16(c0, a + 0, bg + 3 * 64, idesc, 1u);   // q0, x tap 1
+                            }
                         }
                     }
                     tc::mma_commit(&acc_full[b]);
