@@ -133,6 +133,9 @@ __device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
 __device__ __forceinline__ void bar_arrive(uint64_t* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(b)) : "memory");
 }
+// bounded wait (2 s of %globaltimer, the poll count as a backstop); gives up
+// early once another thread has raised the abort flag, where one is given.
+// Each poll may sleep until the phase completes
 __device__ __forceinline__ bool wait_bar(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
     const uint32_t a = tc::smem_u32(b);
     if (mbar_try_wait_sleep(a, parity, kSuspendNs)) return true;
@@ -153,7 +156,6 @@ __device__ __forceinline__ void tma_snap(float* dst, const CUtensorMap* map, int
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(tc::smem_u32(bar))
         : "memory");
 }
-
 
 // 16 columns at a TMEM address (one M tile) of this warp's lanes into r,
 // without waiting: the registers must not be read before tmem_wait_regs(r)
