@@ -41,6 +41,7 @@
 #include <algorithm>
 
 #include "ae_internal.h"
+#include "packed_f32x2.cuh"
 #include "tc_gemm.cuh"
 #include "tma_encode.h"
 #include "wait_clock.cuh"
@@ -90,7 +91,7 @@ __device__ __forceinline__ void taps(int q, int tau, int& t, int& k) {
     }
 }
 
-__device__ __forceinline__ float lrelu(float a) { return a > 0.f ? a : kSlope * a; }
+static_assert(kSlope > 0.f && kSlope < 1.f, "LeakyReLU as a maximum needs 0 < slope < 1");
 
 // KB block of the B operand of (parity q, tap tau) in the W3 table: per
 // x-parity pair m = q >> 1 and tap group g = tau >> 1 (z, y tap bits), four
@@ -359,7 +360,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float sc = A.sigma ? *A.sigma : 1.0f;
         const bool vec = ((reinterpret_cast<uintptr_t>(A.out.p) & 15) == 0) &&
                          (A.out.sy % 4 == 0) && (A.out.sz % 4 == 0);
-        const float4* b3v = reinterpret_cast<const float4*>(b3s);
+        // b3 as packed pairs and the slope as a pair (f32x2 arithmetic, IEEE
+        // single precision per lane)
+        uint64_t b3p[16];
+#pragma unroll
+        for (int c = 0; c < 16; c++) b3p[c] = f32x2::pack(b3s[2 * c], b3s[2 * c + 1]);
+        const uint64_t slope2 = f32x2::pack(kSlope, kSlope);
         uint8_t* atile = a2 + g * 4 * kA2Bytes;  // this warpgroup's four D2 A operands
         constexpr uint32_t idesc2 = tc::idesc_bf16(128, 16);
         int out = 0, d2_phase = 0;
@@ -380,43 +386,52 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
                 for (int qz = 0; qz < 2 && ok; qz++) {
                     // g1 = bf16(LeakyReLU(acc + b3)) of the four parities (qz, qy, qx)
-                    // into the A operands (row = latent voxel, K = channel)
-#pragma unroll 1
-                    for (int qy = 0; qy < 2; qy++) {
-                        const int qzy = qz * 2 + qy;
-                        uint32_t r0[32], r1[32];
-                        tmem_ld16_nw(tb + (qzy * 2) * 32, r0);
-                        tmem_ld16_nw(tb + (qzy * 2) * 32 + 16, r0 + 16);
-                        tmem_ld16_nw(tb + (qzy * 2 + 1) * 32, r1);
-                        tmem_ld16_nw(tb + (qzy * 2 + 1) * 32 + 16, r1 + 16);
-                        tmem_wait_regs16(r0);
-                        tmem_wait_regs16(r0 + 16);
-                        tmem_wait_regs16(r1);
-                        tmem_wait_regs16(r1 + 16);
-                        float a0[32], a1[32];
-#pragma unroll
-                        for (int i = 0; i < 32; i++) {
-                            a0[i] = __uint_as_float(r0[i]);
-                            a1[i] = __uint_as_float(r1[i]);
-                        }
-#pragma unroll
-                        for (int c4 = 0; c4 < 8; c4++) {
-                            const float4 bb = b3v[c4];
-                            const float b_[4] = {bb.x, bb.y, bb.z, bb.w};
-#pragma unroll
-                            for (int i = 0; i < 4; i++) {
-                                a0[4 * c4 + i] = lrelu(a0[4 * c4 + i] + b_[i]);
-                                a1[4 * c4 + i] = lrelu(a1[4 * c4 + i] + b_[i]);
-                            }
-                        }
-                        uint8_t* t0 = atile + (qy * 2) * kA2Bytes;
-                        uint8_t* t1 = t0 + kA2Bytes;
+                    // into the A operands (row = latent voxel, K = channel), one
+                    // parity's TMEM load in flight while the one before it is
+                    // processed; LeakyReLU as max(h, slope h) on packed pairs (the
+                    // same bits as the select form for 0 < slope < 1)
+                    auto tile = [&](int p4, const uint32_t* r) {
+                        uint8_t* t = atile + p4 * kA2Bytes;
 #pragma unroll
                         for (int k8 = 0; k8 < 4; k8++) {
-                            tc::st_vec8(t0, row, 8 * k8, tc::pack8(a0 + 8 * k8));
-                            tc::st_vec8(t1, row, 8 * k8, tc::pack8(a1 + 8 * k8));
+                            uint32_t w[4];
+#pragma unroll
+                            for (int c = 0; c < 4; c++) {
+                                const int i = 8 * k8 + 2 * c;
+                                const uint64_t h = f32x2::add(
+                                    f32x2::pack(__uint_as_float(r[i]), __uint_as_float(r[i + 1])),
+                                    b3p[i >> 1]);
+                                const uint64_t sh = f32x2::mul(h, slope2);
+                                float h0, h1, s0, s1;
+                                f32x2::unpack(h, h0, h1);
+                                f32x2::unpack(sh, s0, s1);
+                                w[c] = tc::pack2(fmaxf(h0, s0), fmaxf(h1, s1));
+                            }
+                            tc::st_vec8(t, row, 8 * k8, make_uint4(w[0], w[1], w[2], w[3]));
                         }
-                    }
+                    };
+                    const uint32_t cq = tb + qz * 4 * 32;
+                    uint32_t x0[32], x1[32];
+                    tmem_ld16_nw(cq, x0);
+                    tmem_ld16_nw(cq + 16, x0 + 16);
+                    tmem_wait_regs16(x0);
+                    tmem_wait_regs16(x0 + 16);
+                    tmem_ld16_nw(cq + 32, x1);
+                    tmem_ld16_nw(cq + 48, x1 + 16);
+                    tile(0, x0);
+                    tmem_wait_regs16(x1);
+                    tmem_wait_regs16(x1 + 16);
+                    tmem_ld16_nw(cq + 64, x0);
+                    tmem_ld16_nw(cq + 80, x0 + 16);
+                    tile(1, x1);
+                    tmem_wait_regs16(x0);
+                    tmem_wait_regs16(x0 + 16);
+                    tmem_ld16_nw(cq + 96, x1);
+                    tmem_ld16_nw(cq + 112, x1 + 16);
+                    tile(2, x0);
+                    tmem_wait_regs16(x1);
+                    tmem_wait_regs16(x1 + 16);
+                    tile(3, x1);
                     // the generic-proxy tile writes and the drained accumulator
                     // columns, then one thread issues the D2 products into those
                     // columns: [128 x 32] g1 x [32 x 16] W4 (rows 8..15 zero)
