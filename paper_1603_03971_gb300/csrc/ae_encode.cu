@@ -7,21 +7,20 @@
 // planes z. Latent plane z reads h1 planes 2z - 1, 2z, 2z + 1; each h1 plane
 // of the column is a 17 x 33 tile (one h1 voxel of halo on the low side)
 // computed from two snapshot planes, which TMA copies (40 x 66 floats, zeros
-// outside the volume) into a three-slot ring; a loader thread (warp 21)
+// outside the volume) into a three-slot ring; a loader thread (warp 13)
 // issues each copy as soon as its slot is free.
 //
-// E1 runs on the tensor cores as well. Two E1 roles of 256 threads (warps
-// 1-8: even h1 planes, warps 9-16: odd ones) each write, for their plane,
+// E1 runs on the tensor cores as well. Two E1 roles of 128 threads (warps
+// 1-4: even h1 planes, warps 5-8: odd ones) each write, for their plane,
 // the bf16(s / rms) values of every h1 voxel's 2 x 2 x 2 patch as one row of
 // a 648-row A tile (rows in h1 slot order, below: row 17 iy + slot, so that
 // one float4 of the snapshot row serves two voxels and the epilogue's
-// stores are contiguous); once all 256 rows are in (mbarrier of 256
-// arrivals) the role's first thread issues 5 tcgen05.mma (M = 128 voxels,
+// stores are contiguous); once all 128 threads have written their rows
+// (mbarrier of 128 arrivals) the role's first thread issues 5 tcgen05.mma (M = 128 voxels,
 // N = 32, K = 16: the 8 patch values, then 8 columns multiplied by the zero
 // half of W1) into the role's 160 TMEM columns. Each warp of a role reads
-// its 32 TMEM lanes of 16 of the 32 channels (the role's first warpgroup
-// channels 0-15, the second 16-31), one M tile loading while the one before
-// it is processed, adds b1, applies LeakyReLU (packed f32x2 arithmetic),
+// the 32 channels of its 32 TMEM lanes, one M tile loading while the one
+// before it is processed, adds b1, applies LeakyReLU (packed f32x2 arithmetic),
 // rounds to bf16 and stores h1 into a three-slot ring laid out as E2's A
 // operand in the canonical K-major no-swizzle layout: four 8-channel
 // core-matrix columns (leading byte offset 8976 B) of [33][17] 16-byte
@@ -41,18 +40,21 @@
 // so each latent sums its 27 taps in the order of the GEMM-engine encoder
 // and each h1 slot is freed after one use. Two 16-column accumulators
 // (TMEM columns 0-15 and 16-31) alternate between latent planes; warps
-// 17-20 add b2, round to bf16 and store the latent rows. mbarriers:
-// snapshot full (TMA bytes) / free (256 arrivals), A tile full (256
-// arrivals) / E1 done (commit), h1 full (256 arrivals) / free (commit),
+// 9-12 add b2, round to bf16 and store the latent rows. mbarriers:
+// snapshot full (TMA bytes) / free (128 arrivals), A tile full (128
+// arrivals) / E1 done (commit), h1 full (128 arrivals) / free (commit),
 // accumulator full (commit) / free (128 arrivals). Every wait is bounded,
 // shares an abort flag and sleeps in the mbarrier poll instead of spinning.
 //
-// Measured with per-stage clock stamps at 384^3 (one h1 plane every ~2700
+// Measured with per-stage clock stamps at 384^3 (one h1 plane every ~2600
 // cycles per CTA): a single issuing thread for E1 and E2, snapshot copies
-// and E2 MMAs in one event loop, and one warpgroup per E1 role made the E1
-// MMAs wait ~1900 cycles per plane behind the E2 issue and the epilogue of
-// one plane take ~4000 cycles; pairing the kz = 2 and kz = 0 MMAs cut the
-// E2 issue from ~2060 to ~1560 cycles per plane.
+// and E2 MMAs in one event loop made the E1 MMAs wait ~1900 cycles per plane
+// behind the E2 issue, and the epilogue of one plane took ~4000 cycles with
+// unpipelined TMEM loads and scalar arithmetic; pairing the kz = 2 and
+// kz = 0 MMAs cut the E2 issue from ~2060 to ~1560 cycles per plane. With
+// the epilogue pipelined and packed, roles of one warpgroup (14 warps per
+// SM) run 2 % faster than roles of two warpgroups (22 warps) that split the
+// channels.
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -79,7 +81,7 @@ constexpr int NVOX = HX * HY;           // 561
 constexpr int kRowBytes = HX * 16;      // one h1 row of one 8-channel column: 272 B
 constexpr int kKcBytes = HY * kRowBytes;                 // 8976 B
 constexpr int kH1Bytes = 35968;                          // 4 columns (35904 B), 128-aligned
-static_assert(32 * kRowBytes + 16 * 16 + 2 * kKcBytes < 65536, "h1 row offsets fit 16 bits");
+static_assert(32 * kRowBytes + 16 * 16 < 65536, "h1 row offsets fit 16 bits");
 constexpr int SX = 40, SYR = 2 * HY;                     // snapshot box: 40 x 66 x 2
 constexpr int kSnapBytes = SX * SYR * 2 * 4;             // 21120
 // E2 B operands, per (tap t9 of a kz, K half): region C holds kz = 2 and 0
@@ -96,8 +98,8 @@ constexpr int kE1Col = 32;          // E1 accumulators: 2 x (5 x 32) TMEM column
 constexpr int kSmem = 128 + kW2Bytes + kW1Bytes + kSS * kSnapBytes + kSH * kH1Bytes +
                       2 * kATileBytes;
 static_assert(kSmem + 1024 <= 227 * 1024, "shared memory of one CTA");
-constexpr int kE1Threads = 256;   // threads of one E1 role (two warpgroups)
-constexpr int kThreads = 22 * 32;
+constexpr int kE1Threads = 128;  // threads of one E1 role (one warpgroup)
+constexpr int kThreads = 14 * 32;
 constexpr int kTmemCols = 512;
 constexpr long long kLimit = 1LL << 24;
 constexpr uint32_t kSuspendNs = 20000;  // longest sleep of one poll (woken by the phase)
@@ -389,25 +391,24 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc::mma_commit(&fin);
             if (!wait_bar(&fin, 0, nullptr)) *abrt = 1;
         }
-    } else if (warp <= 16) {
-        // ---------------- E1: two roles of 8 warps, alternate h1 planes ----------------
+    } else if (warp <= 8) {
+        // ---------------- E1: two roles of 4 warps, alternate h1 planes ----------------
         // per plane: A tile rows = bf16(s / rms) of each h1 voxel's 2 x 2 x 2 patch;
         // the role's first thread puts W1 x0 into the role's TMEM columns; the
         // epilogue adds b1, applies LeakyReLU, rounds to bf16 and stores h1.
-        // Role g = warps 1 + 8 g .. 8 + 8 g; a warp reads TMEM lanes 32 (warp % 4)
-        // .. + 31 and h1 channels 16 hc .. 16 hc + 15 (hc: its warpgroup in the role)
-        const int g = (warp - 1) >> 3, t = tid - 32 - kE1Threads * g, q = warp & 3;
-        const int hc = ((warp - 1) >> 2) & 1;
+        // Role g = warps 1 + 4 g .. 4 + 4 g; a warp reads TMEM lanes 32 (warp % 4)
+        // .. + 31, all 32 h1 channels
+        const int g = (warp - 1) >> 2, t = tid - 32 - kE1Threads * g, q = warp & 3;
         uint8_t* at = atile + g * kATileBytes;
-        const uint32_t tcol = tmem + kE1Col + g * 160 + 16 * hc + ((uint32_t)(q * 32) << 16);
+        const uint32_t tcol = tmem + kE1Col + g * 160 + ((uint32_t)(q * 32) << 16);
         constexpr uint32_t idesc1 = tc::idesc_bf16(128, 32);
         const uint64_t dW1 = tc::sdesc(tc::smem_u32(w1), 128, 256);
-        // b1 of this warp's 16 channels as pairs, and the slope as a pair:
+        // b1 as pairs, and the slope as a pair:
         // packed f32x2 adds and multiplies (IEEE single precision per lane)
-        uint64_t b1p[8];
+        uint64_t b1p[16];
 #pragma unroll
-        for (int c = 0; c < 8; c++)
-            b1p[c] = f32x2::pack(A.P[kOB1 + 16 * hc + 2 * c], A.P[kOB1 + 16 * hc + 2 * c + 1]);
+        for (int c = 0; c < 16; c++)
+            b1p[c] = f32x2::pack(A.P[kOB1 + 2 * c], A.P[kOB1 + 2 * c + 1]);
         const uint64_t slope2 = f32x2::pack(kSlope, kSlope);
         const float inv_s = *A.inv_sigma;
         // per item: this thread's h1 row offset in each M tile (16 bits each,
@@ -433,8 +434,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int iy = r / HX, sl = r - iy * HX;
                     const int ix = sl < 9 ? 2 * sl : 2 * sl - 17;
                     const int hy = 32 * cy - 1 + iy, hx = 16 * cx - 1 + ix;
-                    tile_off[mt >> 1] |= (uint32_t)(iy * kRowBytes + sl * 16 + 2 * hc * kKcBytes)
-                                         << (16 * (mt & 1));
+                    tile_off[mt >> 1] |= (uint32_t)(iy * kRowBytes + sl * 16) << (16 * (mt & 1));
                     if (r < NVOX && hy >= 0 && hy < A.h.ny && hx >= 0 && hx < A.h.nx)
                         in_xy |= 1u << mt;
                 }
@@ -492,59 +492,73 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc::tc_fence_after();
             uint8_t* hp = h1 + (j % kSH) * kH1Bytes;
             const bool zin = hz >= 0 && hz < A.h.nz;
-            // one M tile's 16 channels: b1, LeakyReLU as max(h, slope h) (the
-            // same bits as the select form for 0 < slope < 1), bf16, two
+            // one M tile's 32 channels: b1, LeakyReLU as max(h, slope h) (the
+            // same bits as the select form for 0 < slope < 1), bf16, four
             // 16-byte stores; consecutive lanes hold consecutive slots, so the
-            // stores are conflict-free
+            // stores are conflict-free. Each tile after the first loads while
+            // the one before it is stored (a loaded register becomes readable
+            // a few hundred cycles after the load is issued); tiles 0-3 hold
+            // rows of every warp (row 384 + 127 < 561), tile 4 only those of
+            // the warps whose rows start below 561
             auto store_tile = [&](int mt, const uint32_t* acc) {
                 if (mt * 128 + q * 32 + lane >= NVOX) return;
                 const bool in = zin && ((in_xy >> mt) & 1u);
                 uint8_t* dst = hp + ((tile_off[mt >> 1] >> (16 * (mt & 1))) & 0xFFFFu);
-                uint32_t w[8];  // every value first, then the two stores
 #pragma unroll
-                for (int c = 0; c < 8; c++) {
-                    const uint64_t h = f32x2::add(
-                        f32x2::pack(__uint_as_float(acc[2 * c]), __uint_as_float(acc[2 * c + 1])),
-                        b1p[c]);
-                    const uint64_t sh = f32x2::mul(h, slope2);
-                    float h0, h1, s0, s1;
-                    f32x2::unpack(h, h0, h1);
-                    f32x2::unpack(sh, s0, s1);
-                    w[c] = in ? tc::pack2(fmaxf(h0, s0), fmaxf(h1, s1)) : 0u;
+                for (int kc = 0; kc < 4; kc++) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int c = 0; c < 4; c++) {
+                        const int i = 8 * kc + 2 * c;
+                        const uint64_t h = f32x2::add(
+                            f32x2::pack(__uint_as_float(acc[i]), __uint_as_float(acc[i + 1])),
+                            b1p[i >> 1]);
+                        const uint64_t sh = f32x2::mul(h, slope2);
+                        float h0, h1, s0, s1;
+                        f32x2::unpack(h, h0, h1);
+                        f32x2::unpack(sh, s0, s1);
+                        w[c] = in ? tc::pack2(fmaxf(h0, s0), fmaxf(h1, s1)) : 0u;
+                    }
+                    *reinterpret_cast<uint4*>(dst + kc * kKcBytes) = make_uint4(w[0], w[1], w[2], w[3]);
                 }
-                *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
-                *reinterpret_cast<uint4*>(dst + kKcBytes) = make_uint4(w[4], w[5], w[6], w[7]);
             };
-            // tiles 0-3 hold rows of every warp (row 384 + 127 < 561); tile 4
-            // only those of the warps whose rows start below 561. Each tile
-            // after the first two loads while the one before it is stored (a
-            // loaded register becomes readable a few hundred cycles after the
-            // load is issued)
             const bool t4 = 4 * 128 + q * 32 < NVOX;  // warp-uniform
-            uint32_t x0[16], x1[16], x2[16];
+            uint32_t x0[32], x1[32];
             tmem_ld16_nw(tcol, x0);
+            tmem_ld16_nw(tcol + 16, x0 + 16);
+            tmem_wait_regs(x0);
+            tmem_wait_regs(x0 + 16);
             tmem_ld16_nw(tcol + 32, x1);
-            tmem_wait_regs(x0);
-            tmem_wait_regs(x1);
-            tmem_ld16_nw(tcol + 64, x2);
+            tmem_ld16_nw(tcol + 48, x1 + 16);
             store_tile(0, x0);
+            tmem_wait_regs(x1);
+            tmem_wait_regs(x1 + 16);
+            tmem_ld16_nw(tcol + 64, x0);
+            tmem_ld16_nw(tcol + 80, x0 + 16);
             store_tile(1, x1);
-            tmem_wait_regs(x2);
-            tmem_ld16_nw(tcol + 96, x0);
-            store_tile(2, x2);
             tmem_wait_regs(x0);
-            if (t4) tmem_ld16_nw(tcol + 128, x1);
-            store_tile(3, x0);
+            tmem_wait_regs(x0 + 16);
+            tmem_ld16_nw(tcol + 96, x1);
+            tmem_ld16_nw(tcol + 112, x1 + 16);
+            store_tile(2, x0);
+            tmem_wait_regs(x1);
+            tmem_wait_regs(x1 + 16);
             if (t4) {
-                tmem_wait_regs(x1);
-                store_tile(4, x1);
+                tmem_ld16_nw(tcol + 128, x0);
+                tmem_ld16_nw(tcol + 144, x0 + 16);
+            }
+            store_tile(3, x1);
+            if (t4) {
+                tmem_wait_regs(x0);
+                tmem_wait_regs(x0 + 16);
+                store_tile(4, x0);
             }
             tc::tc_fence_before();
             tc::fence_proxy_async();
             bar_arrive(&h1_full[j % kSH]);
         }
-    } else if (warp <= 20) {
-        // ---------------- latent epilogue: warps 17-20 ----------------
+    } else if (warp <= 12) {
+        // ---------------- latent epilogue: warps 9-12 ----------------
         const int row = tid & 127, ly = row >> 3, lx = row & 7;
         const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
         float b2[16];
@@ -576,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else if (lane == 0) {
-        // ---------------- snapshot loader: warp 21 ----------------
+        // ---------------- snapshot loader: warp 13 ----------------
         // each h1 plane's two snapshot planes into the next ring slot once
         // the role that used the slot last has built its A tile from it
         int np = 0;  // h1 planes of this CTA
