@@ -153,3 +153,14 @@ def test_workspace_sizes_follow_the_storage_policy():
     assert band == nx * ny * nz - (nx - 2 * r) * (ny - 2 * r) * (nz - 2 * r)
     b = rtm.workspace_size(_p(nt=nt, storage="boundary"))
     assert 4 * (4 * N + slab + (nt - 2) * band) <= b < 4 * (4 * N + slab + (nt - 2) * band) + 64 * 256
+
+
+def test_test_stall_arms_and_disarms_without_a_device():
+    """rtm_set_test_stall is host state only: it accepts the two kernels,
+    arming (plane >= 0) and disarming (-1), and rejects an unknown kernel."""
+    for kernel in (rtm.STALL_STENCIL, rtm.STALL_ENCODER):
+        rtm.set_test_stall(kernel, 0)
+        rtm.set_test_stall(kernel, -1)
+    with pytest.raises(_lib.RtmError) as e:
+        rtm.set_test_stall(7, 0)
+    assert e.value.code == 1  # RTM_ERR_INVALID
