@@ -440,7 +440,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             const int hz = 2 * z0 - 1 + C.k;
-            ok = wait_bar(&snap_full[j % kSS], (uint32_t)((j / kSS) & 1), abrt);
+            // the slot's previous plane (the other role's) released first: then
+            // its copy has landed, and this wait's parity names this plane's
+            // phase and not that earlier, still incomplete one
+            ok = j < kSS || wait_bar(&snap_free[j % kSS], (uint32_t)((j / kSS - 1) & 1), abrt);
+            if (ok) ok = wait_bar(&snap_full[j % kSS], (uint32_t)((j / kSS) & 1), abrt);
             if (!ok) break;
             const float* sp = snap + (j % kSS) * (kSnapBytes / 4);
             // A tile rows in h1 slot order: row 17 iy + slot. Unit (iy, p) reads
